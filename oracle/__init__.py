@@ -1,0 +1,189 @@
+"""CPU oracle for the integral histogram -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+legs may import this package.  The product library (``paper_1711_01919_gb300``)
+never imports it, and the two share no code.
+
+The arithmetic lives in ``ihist_oracle.c`` (plain single-threaded C following
+Eq. 1 / Algorithm 1 and Eq. 2 of arXiv 1711.01919, Sec. 2.1).  This module only
+compiles that file with gcc (on first use, or from ``build()``) and marshals
+numpy arrays through ctypes.
+
+Functions (module level, on the default build)
+---------------------------------------------
+bin_of(v, nbins)                  Q of Eq. 1: the uniform bin of intensity v.
+integral_histogram(img, nbins)    Algorithm 1 over all bins -> [nbins][h][w] uint32.
+integral_histogram_plane(img, nbins, k)   one bin plane of Algorithm 1.
+integral_histogram_threads(img, nbins, nthreads)  same result, bins split over
+                                  threads (timing only; Sec. 4.7 methodology).
+query(hist, rects)                Eq. 2 on an inclusive rect list -> [n][nbins].
+region_brute(img, nbins, rect)    direct count over a rectangle (no Eq. 2).
+
+``Oracle(path)`` wraps any shared object built from ``ihist_oracle.c``; the
+tests use it to load deliberately mutated copies and check that the pins
+reject them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SOURCE = os.path.join(HERE, "ihist_oracle.c")
+_LIB = os.path.join(HERE, "libihist_oracle.so")
+_lock = threading.Lock()
+_default = None
+
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+def compile_c(src: str, out: str) -> str:
+    """gcc -O2 shared object from one C file (atomic replace)."""
+    tmp = out + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-pthread", src, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile ihist_oracle.c into libihist_oracle.so next to it."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(SOURCE):
+        compile_c(SOURCE, _LIB)
+    return _LIB
+
+
+def _img(img) -> np.ndarray:
+    a = np.asarray(img)
+    if a.dtype != np.uint8 or a.ndim != 2:
+        raise ValueError("image must be a 2-D uint8 array")
+    if a.strides[1] != 1 or a.strides[0] < a.shape[1]:
+        a = np.ascontiguousarray(a)
+    return a
+
+
+def _p8(a):
+    return a.ctypes.data_as(_u8p)
+
+
+def _p32(a):
+    return a.ctypes.data_as(_u32p)
+
+
+class Oracle:
+    """ctypes view of one build of ihist_oracle.c."""
+
+    def __init__(self, path: str):
+        lib = ctypes.CDLL(path)
+        lib.oracle_bin_of.argtypes = [ctypes.c_int, ctypes.c_int]
+        lib.oracle_bin_of.restype = ctypes.c_int
+        lib.oracle_ih_plane.argtypes = [_u8p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, _u32p]
+        lib.oracle_ih_plane.restype = None
+        lib.oracle_ih.argtypes = [_u8p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, _u32p]
+        lib.oracle_ih.restype = None
+        lib.oracle_ih_threads.argtypes = [_u8p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, _u32p, ctypes.c_int]
+        lib.oracle_ih_threads.restype = ctypes.c_int
+        lib.oracle_query.argtypes = [_u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     _i32p, ctypes.c_int, _u32p]
+        lib.oracle_query.restype = ctypes.c_int
+        lib.oracle_region_brute.argtypes = [_u8p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, _u32p]
+        lib.oracle_region_brute.restype = ctypes.c_int
+        self.lib = lib
+        self.path = path
+
+    def bin_of(self, v: int, nbins: int) -> int:
+        """Q of Eq. 1 for one intensity value."""
+        return int(self.lib.oracle_bin_of(int(v), int(nbins)))
+
+    def integral_histogram(self, img, nbins: int) -> np.ndarray:
+        """Algorithm 1: the [nbins][h][w] uint32 integral histogram of img."""
+        a = _img(img)
+        h, w = a.shape
+        out = np.empty((nbins, h, w), dtype=np.uint32)
+        if h and w and nbins:
+            self.lib.oracle_ih(_p8(a), a.strides[0], h, w, nbins, _p32(out))
+        return out
+
+    def integral_histogram_plane(self, img, nbins: int, k: int, out=None) -> np.ndarray:
+        """Bin plane k of Algorithm 1, [h][w] uint32."""
+        a = _img(img)
+        h, w = a.shape
+        if out is None:
+            out = np.empty((h, w), dtype=np.uint32)
+        if out.shape != (h, w) or out.dtype != np.uint32 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous uint32 [h][w] array")
+        if h and w:
+            self.lib.oracle_ih_plane(_p8(a), a.strides[0], h, w, nbins, k, _p32(out))
+        return out
+
+    def integral_histogram_threads(self, img, nbins: int, nthreads: int, out=None):
+        """Bins-parallel run of Algorithm 1; returns (hist, threads_used)."""
+        a = _img(img)
+        h, w = a.shape
+        if out is None:
+            out = np.empty((nbins, h, w), dtype=np.uint32)
+        used = self.lib.oracle_ih_threads(_p8(a), a.strides[0], h, w, nbins, _p32(out), int(nthreads))
+        return out, int(used)
+
+    def query(self, hist: np.ndarray, rects) -> np.ndarray:
+        """Eq. 2 for each inclusive rect (x0, y0, x1, y1); out-of-range rects give zeros."""
+        hist = np.ascontiguousarray(hist, dtype=np.uint32)
+        nbins, h, w = hist.shape
+        r = np.ascontiguousarray(np.asarray(rects, dtype=np.int32).reshape(-1, 4))
+        out = np.zeros((r.shape[0], nbins), dtype=np.uint32)
+        if r.shape[0]:
+            self.lib.oracle_query(_p32(hist), h, w, nbins, r.ctypes.data_as(_i32p), r.shape[0], _p32(out))
+        return out
+
+    def region_brute(self, img, nbins: int, rect) -> np.ndarray:
+        """Histogram of the pixels inside an inclusive rect, counted directly."""
+        a = _img(img)
+        h, w = a.shape
+        x0, y0, x1, y1 = (int(v) for v in rect)
+        out = np.zeros(nbins, dtype=np.uint32)
+        self.lib.oracle_region_brute(_p8(a), a.strides[0], h, w, nbins, x0, y0, x1, y1, _p32(out))
+        return out
+
+
+def default() -> Oracle:
+    """The oracle built from ihist_oracle.c as committed."""
+    global _default
+    with _lock:
+        if _default is None:
+            _default = Oracle(build())
+    return _default
+
+
+def bin_of(v, nbins):
+    return default().bin_of(v, nbins)
+
+
+def integral_histogram(img, nbins):
+    return default().integral_histogram(img, nbins)
+
+
+def integral_histogram_plane(img, nbins, k, out=None):
+    return default().integral_histogram_plane(img, nbins, k, out)
+
+
+def integral_histogram_threads(img, nbins, nthreads, out=None):
+    return default().integral_histogram_threads(img, nbins, nthreads, out)
+
+
+def query(hist, rects):
+    return default().query(hist, rects)
+
+
+def region_brute(img, nbins, rect):
+    return default().region_brute(img, nbins, rect)

@@ -1,0 +1,162 @@
+/*
+ * ihist_oracle.c -- CPU oracle for the integral histogram.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
+ * calls this file: only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / --impl reference legs use it.  It shares no code, header,
+ * table or constant with the CUDA library in paper_1711_01919_gb300/csrc.
+ *
+ * What it computes (Poostchi et al., "Fast Integral Histogram Computations on
+ * GPU for Real-Time Video Analytics", arXiv 1711.01919):
+ *
+ *   H(x, y, b) = sum_{r<=x} sum_{c<=y} Q(I(r, c), b)                  (Eq. 1)
+ *
+ * computed with the sequential recurrence of Algorithm 1 (Sec. 2.1):
+ *
+ *   H(k, x, y) = H(k, x-1, y) + H(k, x, y-1) - H(k, x-1, y-1) + Q(k, I(x, y))
+ *
+ * looping over bins k, then rows x, then columns y.  The paper's x is the
+ * row index and y the column index (Alg. 1 runs x over h and y over w).
+ *
+ * Readings taken where the paper is silent or ambiguous:
+ *   - 0-based indices; any term with index -1 is zero (Alg. 1 is 1-based
+ *     with an implicit zero border).
+ *   - inclusive sums: a pixel counts in its own H (Eq. 1 sums r<=x, c<=y).
+ *   - Q(v, b) = 1 iff floor(v * B / 256) == b for uint8 v and B uniform bins
+ *     (the paper leaves the bin edges open, Sec. 2.1).
+ *   - output layout [b][row][col] row-major, uint32 counts ("4 byte integer",
+ *     Sec. 4.6; 3-D array mapped row-major to 1-D, Sec. 3.1 / Fig. 2).
+ *   - region query (Eq. 2) for an inclusive rectangle (x0, y0, x1, y1) with
+ *     x = column, y = row:
+ *       h = H[y1][x1] - H[y0-1][x1] - H[y1][x0-1] + H[y0-1][x0-1]
+ *     with index -1 terms zero, evaluated in uint32 modular arithmetic
+ *     (the true result lies in [0, area], so intermediate wrap is harmless).
+ *
+ * Every function is plain, single-threaded and unblocked, except
+ * oracle_ih_threads(), the bins-parallel variant used only to time the CPU
+ * with all host cores (the paper's multi-threaded CPU comparison, Sec. 4.7);
+ * it runs the same per-plane function on disjoint bins.
+ */
+#include <pthread.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+/* Binning function Q of Eq. 1 (Sec. 2.1): the bin of intensity v among
+ * nbins uniform bins over [0, 256). */
+int oracle_bin_of(int v, int nbins) { return (v * nbins) / 256; }
+
+/* One bin plane k of Algorithm 1.  img: h rows of w bytes, row stride pitch.
+ * plane: [h][w] uint32, fully overwritten. */
+void oracle_ih_plane(const uint8_t *img, size_t pitch, int h, int w, int nbins,
+                     int k, uint32_t *plane) {
+  for (int x = 0; x < h; ++x) {
+    for (int y = 0; y < w; ++y) {
+      uint32_t above = (x > 0) ? plane[(size_t)(x - 1) * w + y] : 0u;
+      uint32_t left = (y > 0) ? plane[(size_t)x * w + (y - 1)] : 0u;
+      uint32_t diag = (x > 0 && y > 0) ? plane[(size_t)(x - 1) * w + (y - 1)] : 0u;
+      uint32_t q = (oracle_bin_of(img[(size_t)x * pitch + y], nbins) == k) ? 1u : 0u;
+      plane[(size_t)x * w + y] = above + left - diag + q;
+    }
+  }
+}
+
+/* Algorithm 1 over all bins: out is [nbins][h][w] uint32. */
+void oracle_ih(const uint8_t *img, size_t pitch, int h, int w, int nbins,
+               uint32_t *out) {
+  for (int k = 0; k < nbins; ++k)
+    oracle_ih_plane(img, pitch, h, w, nbins, k, out + (size_t)k * h * w);
+}
+
+/* Region histogram by Eq. 2 from a bin-major integral histogram hist
+ * ([nbins][h][w]).  rects: n x {x0, y0, x1, y1}, inclusive, x = column.
+ * out: [n][nbins].  Returns the number of rectangles that were out of range
+ * (those get an all-zero histogram). */
+int oracle_query(const uint32_t *hist, int h, int w, int nbins,
+                 const int32_t *rects, int n, uint32_t *out) {
+  int bad = 0;
+  for (int i = 0; i < n; ++i) {
+    int x0 = rects[4 * i + 0], y0 = rects[4 * i + 1];
+    int x1 = rects[4 * i + 2], y1 = rects[4 * i + 3];
+    int ok = (0 <= x0 && x0 <= x1 && x1 < w && 0 <= y0 && y0 <= y1 && y1 < h);
+    for (int b = 0; b < nbins; ++b) {
+      uint32_t r = 0u;
+      if (ok) {
+        const uint32_t *P = hist + (size_t)b * h * w;
+        uint32_t br = P[(size_t)y1 * w + x1];
+        uint32_t tr = (y0 > 0) ? P[(size_t)(y0 - 1) * w + x1] : 0u;
+        uint32_t bl = (x0 > 0) ? P[(size_t)y1 * w + (x0 - 1)] : 0u;
+        uint32_t tl = (y0 > 0 && x0 > 0) ? P[(size_t)(y0 - 1) * w + (x0 - 1)] : 0u;
+        r = br - tr - bl + tl;
+      }
+      out[(size_t)i * nbins + b] = r;
+    }
+    if (!ok) ++bad;
+  }
+  return bad;
+}
+
+/* Brute-force region histogram: counts the pixels of the rectangle directly
+ * (the definition of a histogram over R, Sec. 2.1); independent of Eq. 2.
+ * out: [nbins].  Returns 0, or -1 for an out-of-range rectangle. */
+int oracle_region_brute(const uint8_t *img, size_t pitch, int h, int w,
+                        int nbins, int x0, int y0, int x1, int y1,
+                        uint32_t *out) {
+  for (int b = 0; b < nbins; ++b) out[b] = 0u;
+  if (!(0 <= x0 && x0 <= x1 && x1 < w && 0 <= y0 && y0 <= y1 && y1 < h)) return -1;
+  for (int r = y0; r <= y1; ++r)
+    for (int c = x0; c <= x1; ++c) out[oracle_bin_of(img[(size_t)r * pitch + c], nbins)] += 1u;
+  return 0;
+}
+
+/* ---- bins-parallel variant, for timing the CPU on all host cores ------ */
+
+typedef struct {
+  const uint8_t *img;
+  size_t pitch;
+  int h, w, nbins, first, stride;
+  uint32_t *out;
+} oracle_job_t;
+
+static void *oracle_worker(void *arg) {
+  oracle_job_t *j = (oracle_job_t *)arg;
+  for (int k = j->first; k < j->nbins; k += j->stride)
+    oracle_ih_plane(j->img, j->pitch, j->h, j->w, j->nbins, k,
+                    j->out + (size_t)k * j->h * j->w);
+  return NULL;
+}
+
+/* Same result as oracle_ih(); bins are split round-robin over nthreads
+ * POSIX threads.  Returns the number of threads actually used. */
+int oracle_ih_threads(const uint8_t *img, size_t pitch, int h, int w,
+                      int nbins, uint32_t *out, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > nbins) nthreads = nbins;
+  pthread_t *tid = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+  oracle_job_t *jobs = (oracle_job_t *)malloc(sizeof(oracle_job_t) * (size_t)nthreads);
+  char *running = (char *)calloc((size_t)nthreads, 1);
+  if (!tid || !jobs || !running) {
+    free(tid);
+    free(jobs);
+    free(running);
+    oracle_ih(img, pitch, h, w, nbins, out);
+    return 1;
+  }
+  int started = 0;
+  for (int t = 0; t < nthreads; ++t) {
+    oracle_job_t jb = {img, pitch, h, w, nbins, t, nthreads, out};
+    jobs[t] = jb;
+    if (pthread_create(&tid[t], NULL, oracle_worker, &jobs[t]) == 0) {
+      running[t] = 1;
+      ++started;
+    } else {
+      oracle_worker(&jobs[t]); /* run this share inline */
+    }
+  }
+  for (int t = 0; t < nthreads; ++t)
+    if (running[t]) pthread_join(tid[t], NULL);
+  free(tid);
+  free(jobs);
+  free(running);
+  return started > 0 ? started : 1;
+}

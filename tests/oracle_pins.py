@@ -1,0 +1,268 @@
+"""Pins for the CPU oracle: checks against what the paper and mathematics fix.
+
+Every check takes an ``oracle.Oracle`` so the same suite runs on the oracle as
+committed (test_oracle_pins.py) and on deliberately mutated builds of it
+(test_oracle_mutations.py), where at least one check must fail.
+
+The checks never re-call the oracle's own formula to produce an expected
+value.  Expected values come from:
+  * hand-worked fixtures in tests/golden/ (Eq. 1 and Eq. 2 worked by hand);
+  * brute-force counting in pure Python on tiny frames (Eq. 1 as a count);
+  * invariants that hold for any image: sum over bins = (x+1)(y+1),
+    bottom-right = numpy.bincount of the binned image, monotonicity;
+  * closed forms: constant frame, column ramp, row ramp, single bright pixel;
+  * special cases of the binning: power-of-two B is a right shift, every
+    bin is a contiguous run of width floor(256/B) or ceil(256/B).
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def in_bin(v: int, b: int, nbins: int) -> bool:
+    """v in the b-th of nbins equal sub-intervals of [0, 256): b/B <= v/256 < (b+1)/B."""
+    return 256 * b <= v * nbins < 256 * (b + 1)
+
+
+def brute_bin(v: int, nbins: int) -> int:
+    for b in range(nbins):
+        if in_bin(v, b, nbins):
+            return b
+    raise AssertionError("no bin for %d" % v)
+
+
+def binned(img: np.ndarray, nbins: int) -> np.ndarray:
+    table = np.array([brute_bin(v, nbins) for v in range(256)], dtype=np.int64)
+    return table[img]
+
+
+def brute_integral_histogram(img: np.ndarray, nbins: int) -> np.ndarray:
+    """Eq. 1 as a literal count over the rectangle [0..y] x [0..x] (tiny frames)."""
+    h, w = img.shape
+    bins = [[brute_bin(int(img[r, c]), nbins) for c in range(w)] for r in range(h)]
+    out = np.zeros((nbins, h, w), dtype=np.uint32)
+    for y in range(h):
+        for x in range(w):
+            counts = [0] * nbins
+            for r in range(y + 1):
+                for c in range(x + 1):
+                    counts[bins[r][c]] += 1
+            for b in range(nbins):
+                out[b, y, x] = counts[b]
+    return out
+
+
+def brute_region(img: np.ndarray, nbins: int, rect) -> np.ndarray:
+    x0, y0, x1, y1 = rect
+    out = np.zeros(nbins, dtype=np.uint32)
+    for r in range(y0, y1 + 1):
+        for c in range(x0, x1 + 1):
+            out[brute_bin(int(img[r, c]), nbins)] += 1
+    return out
+
+
+def load_golden(name: str) -> dict:
+    """Parse a hand-worked fixture (see the files for the format)."""
+    lines = [ln.strip() for ln in open(os.path.join(GOLDEN, name)) if ln.strip() and not ln.startswith("#")]
+    d = {"planes": {}, "queries": [], "rest_zero": False}
+    i = 0
+
+    def rows(n):
+        nonlocal i
+        m = [list(map(int, lines[i + k].split())) for k in range(n)]
+        i += n
+        return np.array(m, dtype=np.int64)
+
+    while i < len(lines):
+        tok = lines[i].split()
+        i += 1
+        if tok[0] in ("h", "w", "bins"):
+            d[tok[0]] = int(tok[1])
+        elif tok[0] == "image":
+            d["image"] = rows(d["h"]).astype(np.uint8)
+        elif tok[0] == "H":
+            d["planes"][int(tok[1])] = rows(d["h"])
+        elif tok[0] == "rest":
+            d["rest_zero"] = True
+        elif tok[0] == "query":
+            rect = tuple(int(v) for v in tok[1:5])
+            ans = lines[i].split()
+            i += 1
+            exp = np.zeros(d["bins"], dtype=np.int64)
+            if ans[0] == "sparse":
+                for k in range(1, len(ans), 2):
+                    exp[int(ans[k])] = int(ans[k + 1])
+            else:
+                exp[:] = list(map(int, ans))
+            d["queries"].append((rect, exp))
+        else:
+            raise ValueError("bad fixture line: %r" % (tok,))
+    return d
+
+
+GOLDEN_FILES = ("ih_3x4_b2.txt", "ih_2x4_b3_edges.txt", "ih_2x2_b256.txt")
+TINY_BINS = (1, 2, 3, 5, 8, 32, 256)
+
+
+# ---------------------------------------------------------------- checks
+
+def check_bins(o) -> None:
+    """Q: uniform bins, power-of-two shift, contiguous runs, full range."""
+    for nbins in range(1, 257):
+        got = [o.bin_of(v, nbins) for v in range(256)]
+        assert got[0] == 0 and got[255] == nbins - 1, nbins
+        assert all(got[v] <= got[v + 1] <= got[v] + 1 for v in range(255)), nbins
+        widths = np.bincount(np.array(got), minlength=nbins)
+        assert set(widths.tolist()) <= {256 // nbins, -(-256 // nbins)}, nbins
+        for v in range(256):
+            assert in_bin(v, got[v], nbins), (v, nbins)
+    for k in range(9):
+        nbins = 1 << k
+        for v in range(256):
+            assert o.bin_of(v, nbins) == (v >> (8 - k)), (v, nbins)
+
+
+def check_golden(o) -> None:
+    for name in GOLDEN_FILES:
+        d = load_golden(name)
+        H = o.integral_histogram(d["image"], d["bins"]).astype(np.int64)
+        for b, plane in d["planes"].items():
+            assert np.array_equal(H[b], plane), (name, b)
+        if d["rest_zero"]:
+            others = [b for b in range(d["bins"]) if b not in d["planes"]]
+            assert not H[others].any(), name
+        else:
+            assert sorted(d["planes"]) == list(range(d["bins"])), name
+        for rect, exp in d["queries"]:
+            q = o.query(H.astype(np.uint32), [rect])[0].astype(np.int64)
+            assert np.array_equal(q, exp), (name, rect)
+            r = o.region_brute(d["image"], d["bins"], rect).astype(np.int64)
+            assert np.array_equal(r, exp), (name, rect)
+
+
+def tiny_images():
+    rng = np.random.default_rng(1711)
+    shapes = [(1, 1), (1, 7), (6, 1), (2, 3), (5, 4), (7, 9), (12, 12), (3, 13)]
+    imgs = [rng.integers(0, 256, size=s, dtype=np.uint8) for s in shapes]
+    edge = np.array([[0, 255, 127, 128], [85, 86, 170, 171], [63, 64, 191, 192]], dtype=np.uint8)
+    return imgs + [edge]
+
+
+def check_brute_force(o) -> None:
+    for img in tiny_images():
+        for nbins in TINY_BINS:
+            exp = brute_integral_histogram(img, nbins)
+            got = o.integral_histogram(img, nbins)
+            assert np.array_equal(got, exp), (img.shape, nbins)
+            for k in (0, nbins - 1):
+                assert np.array_equal(o.integral_histogram_plane(img, nbins, k), exp[k])
+
+
+def invariant_errors(img: np.ndarray, nbins: int, H: np.ndarray) -> list:
+    """Properties any correct integral histogram of img satisfies."""
+    errs = []
+    h, w = img.shape
+    Hi = H.astype(np.int64)
+    area = (np.arange(1, h + 1)[:, None] * np.arange(1, w + 1)[None, :])
+    if not np.array_equal(Hi.sum(axis=0), area):
+        errs.append("sum over bins != (x+1)(y+1)")
+    counts = np.bincount(binned(img, nbins).ravel(), minlength=nbins)
+    if not np.array_equal(Hi[:, -1, -1], counts):
+        errs.append("bottom-right != bin counts")
+    if (np.diff(Hi, axis=1) < 0).any() or (np.diff(Hi, axis=2) < 0).any():
+        errs.append("not monotone")
+    first = np.zeros(nbins, dtype=np.int64)
+    first[brute_bin(int(img[0, 0]), nbins)] = 1
+    if not np.array_equal(Hi[:, 0, 0], first):
+        errs.append("H[:,0,0] != one-hot of first pixel")
+    # 2-D second difference recovers the one-hot of each pixel (Alg. 1 solved for Q)
+    P = np.pad(Hi, ((0, 0), (1, 0), (1, 0)))
+    d2 = P[:, 1:, 1:] - P[:, :-1, 1:] - P[:, 1:, :-1] + P[:, :-1, :-1]
+    onehot = (binned(img, nbins)[None, :, :] == np.arange(nbins)[:, None, None]).astype(np.int64)
+    if not np.array_equal(d2, onehot):
+        errs.append("second difference != one-hot")
+    return errs
+
+
+def check_invariants(o) -> None:
+    rng = np.random.default_rng(20171106)
+    for (h, w, nbins) in [(37, 53, 16), (64, 64, 3), (31, 130, 64), (5, 257, 256), (100, 1, 7)]:
+        img = rng.integers(0, 256, size=(h, w), dtype=np.uint8)
+        errs = invariant_errors(img, nbins, o.integral_histogram(img, nbins))
+        assert not errs, (h, w, nbins, errs)
+
+
+def check_closed_forms(o) -> None:
+    h, w = 9, 13
+    area = np.arange(1, h + 1)[:, None] * np.arange(1, w + 1)[None, :]
+    for v, nbins in [(0, 4), (255, 4), (200, 7), (128, 2), (127, 2)]:
+        H = o.integral_histogram(np.full((h, w), v, dtype=np.uint8), nbins).astype(np.int64)
+        b = brute_bin(v, nbins)
+        assert np.array_equal(H[b], area), (v, nbins)
+        assert not np.delete(H, b, axis=0).any(), (v, nbins)
+    # column ramp I(y, x) = x on W = 256: H[b][y][x] = (y+1) * #{x' <= x in bin b}
+    ramp = np.tile(np.arange(256, dtype=np.uint8), (5, 1))
+    for nbins in (1, 3, 8, 100):
+        H = o.integral_histogram(ramp, nbins).astype(np.int64)
+        for b in range(nbins):
+            run = np.cumsum([1 if in_bin(x, b, nbins) else 0 for x in range(256)])
+            assert np.array_equal(H[b], np.arange(1, 6)[:, None] * run[None, :]), (nbins, b)
+    # row ramp (the transposed case): I(y, x) = y on H = 256, width 3
+    H = o.integral_histogram(np.tile(np.arange(256, dtype=np.uint8)[:, None], (1, 3)), 5).astype(np.int64)
+    for b in range(5):
+        run = np.cumsum([1 if in_bin(y, b, 5) else 0 for y in range(256)])
+        assert np.array_equal(H[b], run[:, None] * np.arange(1, 4)[None, :]), b
+    # single bright pixel on a dark frame: H[q][y][x] = [x >= x*][y >= y*]
+    img = np.zeros((11, 17), dtype=np.uint8)
+    img[4, 9] = 250
+    H = o.integral_histogram(img, 8).astype(np.int64)
+    yy, xx = np.mgrid[0:11, 0:17]
+    assert np.array_equal(H[7], ((yy >= 4) & (xx >= 9)).astype(np.int64))
+    assert np.array_equal(H[0], (yy + 1) * (xx + 1) - H[7])
+    # checkerboard of two bins: bin 1 holds floor/ceil halves of every prefix
+    cb = ((np.add.outer(np.arange(8), np.arange(10)) % 2) * 255).astype(np.uint8)
+    H = o.integral_histogram(cb, 2).astype(np.int64)
+    n = (yy[:8, :10] + 1) * (xx[:8, :10] + 1)
+    assert np.array_equal(H[1], n // 2) and np.array_equal(H[0], n - n // 2)
+
+
+def check_query(o) -> None:
+    rng = np.random.default_rng(4)
+    for (h, w, nbins) in [(13, 17, 5), (8, 8, 32), (1, 9, 2), (9, 1, 3), (20, 31, 256)]:
+        img = rng.integers(0, 256, size=(h, w), dtype=np.uint8)
+        H = o.integral_histogram(img, nbins)
+        rects = [(0, 0, w - 1, h - 1), (0, 0, 0, 0), (w - 1, h - 1, w - 1, h - 1)]
+        for _ in range(25):
+            xa, xb = sorted(rng.integers(0, w, size=2).tolist())
+            ya, yb = sorted(rng.integers(0, h, size=2).tolist())
+            rects.append((xa, ya, xb, yb))
+        got = o.query(H, rects)
+        for i, r in enumerate(rects):
+            exp = brute_region(img, nbins, r)
+            assert np.array_equal(got[i], exp), (h, w, nbins, r)
+            assert np.array_equal(o.region_brute(img, nbins, r), exp), (h, w, nbins, r)
+        full = np.bincount(binned(img, nbins).ravel(), minlength=nbins)
+        assert np.array_equal(got[0].astype(np.int64), full)
+    # out-of-range rectangles give zeros and are counted
+    img = rng.integers(0, 256, size=(6, 7), dtype=np.uint8)
+    H = o.integral_histogram(img, 4)
+    bad = [(-1, 0, 2, 2), (0, 0, 7, 1), (3, 2, 2, 2), (0, 4, 1, 3), (0, 0, 0, 6)]
+    assert not o.query(H, bad).any()
+
+
+def check_threads(o) -> None:
+    rng = np.random.default_rng(9)
+    img = rng.integers(0, 256, size=(45, 67), dtype=np.uint8)
+    ref = o.integral_histogram(img, 11)
+    for t in (1, 2, 3, 16):
+        got, used = o.integral_histogram_threads(img, 11, t)
+        assert 1 <= used <= min(t, 11)
+        assert np.array_equal(got, ref), t
+
+
+ALL_CHECKS = (check_bins, check_golden, check_brute_force, check_invariants,
+              check_closed_forms, check_query, check_threads)
