@@ -1,0 +1,158 @@
+/*
+ * ihist.h -- C ABI of libihist.so, a GB300 (sm_103a) integral-histogram
+ * engine for the method of Poostchi et al., "Fast Integral Histogram
+ * Computations on GPU for Real-Time Video Analytics" (arXiv 1711.01919).
+ *
+ * What is computed
+ *   For a uint8 frame I of h rows and w columns and B uniform bins
+ *   Q(v) = floor(v * B / 256), the integral histogram (Eq. 1, Sec. 2.1) is
+ *       H[b][y][x] = #{ (x', y') : x' <= x, y' <= y, Q(I[y'][x']) == b }
+ *   -- the per-bin inclusive 2-D prefix count that Algorithm 1 builds with
+ *   H(k,x,y) = H(k,x-1,y) + H(k,x,y-1) - H(k,x-1,y-1) + Q(k, I(x,y)).
+ *   Row index y runs top to bottom, column index x left to right, origin at
+ *   the top-left corner (Fig. 1).  Counts are exact uint32 ("4 byte integer",
+ *   Sec. 4.6).  The region histogram of an inclusive rectangle is Eq. 2:
+ *       h(R, b) = H[y1][x1] - H[y0-1][x1] - H[y1][x0-1] + H[y0-1][x0-1]
+ *   with every term whose index is -1 taken as zero.
+ *
+ * Conventions for every entry point
+ *   - Pointers named d_* are DEVICE pointers on the plan's device, owned by
+ *     the caller; the library never frees them.  h_* pointers are host
+ *     pointers.  Streams are passed as `void *` holding a cudaStream_t (NULL =
+ *     the legacy default stream).
+ *   - Work is enqueued asynchronously on the stream; the return code reports
+ *     host-side validation and launch errors only.  Errors detected on the
+ *     device (a look-back wait that ran out of time, a bad rectangle) are
+ *     latched in the plan's device status word and read with ihist_status().
+ *   - A plan owns its workspace (allocated once by ihist_plan*); compute and
+ *     query calls allocate nothing.  One plan must not be used by two
+ *     launches that may run concurrently (two streams); create one plan per
+ *     stream.  Calls on one plan from several host threads need external
+ *     locking.
+ *   - Return codes are the IHIST_* values below; nothing aborts or traps.
+ */
+#ifndef IHIST_H
+#define IHIST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return / status codes. */
+enum {
+  IHIST_OK = 0,
+  IHIST_ERR_INVALID_ARG = 1,      /* bad size, pointer, alignment or layout */
+  IHIST_ERR_UNSUPPORTED = 2,      /* valid request outside what this build handles */
+  IHIST_ERR_OOM = 3,              /* workspace allocation failed */
+  IHIST_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+  IHIST_ERR_LOOKBACK_TIMEOUT = 5, /* device: a carry wait ran out of time (result invalid) */
+  IHIST_ERR_BAD_RECT = 6          /* device: a query rectangle was out of range (its row is zero) */
+};
+
+/* Output layouts of H.  Bin-major is the paper's b x h x w tensor mapped
+ * row-major to 1-D (Sec. 3.1, Fig. 2): H[b][y][x] at ((b*h + y)*w + x).
+ * Pixel-major keeps each pixel's B counts together: H[y][x][b] at
+ * ((y*w + x)*B + b), so a region query reads four contiguous vectors. */
+enum { IHIST_BIN_MAJOR = 0, IHIST_PIXEL_MAJOR = 1 };
+
+typedef struct ihist_plan_s *ihist_plan_t;
+
+/* Tile shape of the fused scan kernel.  Zero fields take the library's
+ * default for the frame shape.
+ *   rows_per_band   R, rows one CTA owns (1..255)
+ *   bins_per_cta    G, bins one CTA owns (4, 8 or 16)
+ *   chunks_per_warp m, 128-column chunks one warp owns (1, 2, 4 or 8;
+ *                   at most 2 with bins_per_cta 16);
+ *                   the CTA has ceil(ceil(w/128)/m) warps (at most 16)
+ *   timeout_us      limit of each carry wait before it gives up and latches
+ *                   IHIST_ERR_LOOKBACK_TIMEOUT (default 2,000,000 us)
+ *   fault_skip_band test hook, -1 = off: the CTAs of this band publish no
+ *                   carries, so the band below must time out.  Used only
+ *                   to test failure detection; never set it otherwise.   */
+typedef struct {
+  int rows_per_band;
+  int bins_per_cta;
+  int chunks_per_warp;
+  int ctas_per_sm;   /* persistent grid = ctas_per_sm x SMs (0 = occupancy limit) */
+  unsigned int timeout_us;
+  int fault_skip_band;
+  int reserved[4];
+} ihist_tune_t;
+
+/* Create a plan for frames of h rows x w columns and nbins bins in the given
+ * layout, with default tiling.  Limits: 1 <= h, w <= 65535, h*w < 2^32,
+ * 1 <= nbins <= 256, w <= 16384.  Allocates the plan's device workspace on the
+ * current device.  *out is set only on IHIST_OK. */
+int ihist_plan(int h, int w, int nbins, int layout, ihist_plan_t *out);
+
+/* As ihist_plan with explicit tiling (NULL = defaults). */
+int ihist_plan_tuned(int h, int w, int nbins, int layout, const ihist_tune_t *tune,
+                     ihist_plan_t *out);
+
+/* The tiling a plan resolved to (all fields filled). */
+int ihist_plan_get_tune(ihist_plan_t plan, ihist_tune_t *out);
+
+/* Device workspace bytes the plan holds (carry vectors, flags, control). */
+size_t ihist_workspace_bytes(ihist_plan_t plan);
+
+/* Bytes of one integral histogram: h * w * nbins * 4. */
+size_t ihist_output_bytes(int h, int w, int nbins);
+
+/* Integral histogram of one frame (Eq. 1; fused quantise, row scan, column
+ * scan and carry passing).  d_in: h rows of w bytes, row stride in_pitch
+ * (>= w) bytes.  d_out: ihist_output_bytes(h, w, nbins) bytes in the plan's
+ * layout; every word is written exactly once.  The fast path wants d_in and
+ * in_pitch 4-byte aligned and d_out 16-byte aligned with w % 4 == 0;
+ * anything else takes a slower element-wise path with the same result. */
+int ihist_compute(ihist_plan_t plan, const uint8_t *d_in, size_t in_pitch, uint32_t *d_out,
+                  void *stream);
+
+/* Region histograms by Eq. 2.  d_hist: an integral histogram made by this
+ * plan's layout and shape.  d_rects: n x {x0, y0, x1, y1} int32, inclusive,
+ * x = column.  d_hist_out: n x nbins uint32, row i = histogram of rect i.
+ * A rectangle with x0 > x1, y0 > y1 or a corner outside the frame yields a
+ * zero row and latches IHIST_ERR_BAD_RECT.  n == 0 is a no-op. */
+int ihist_query(ihist_plan_t plan, const uint32_t *d_hist, const int32_t *d_rects, int n,
+                uint32_t *d_hist_out, void *stream);
+
+/* A sequence of frames from HOST memory (the dual-buffered pipeline of
+ * Algorithm 6, Sec. 4.4): frame i+1 is uploaded on copy_stream into one of
+ * two device input slots while frame i is computed on stream.
+ *   h_frames      nframes frames of h x w bytes, frame i at h_frames +
+ *                 i * frame_stride, rows packed (pitch w).  Page-locked
+ *                 memory is needed for the copies to overlap compute.
+ *   d_slots       2 * h * w bytes of device memory (the upload ring).
+ *   d_outs        nouts integral histograms (ihist_output_bytes each, back
+ *                 to back); frame i is written to slot i % nouts.
+ *   d_rects, nrects  optional (nrects may be 0): rectangles queried on every
+ *                 frame's histogram (Eq. 2) into d_query (nrects * nbins
+ *                 uint32) and copied to h_query_out + i * nrects * nbins.
+ * All work is enqueued; the call returns before it finishes.  The caller
+ * synchronises `stream` (which the last copy and compute are ordered on)
+ * before reading h_query_out or reusing h_frames.  Uses two events the
+ * plan owns, so it must not overlap another sequence call on the same plan. */
+int ihist_sequence_host(ihist_plan_t plan, const uint8_t *h_frames, size_t frame_stride,
+                        int nframes, uint8_t *d_slots, uint32_t *d_outs, int nouts,
+                        const int32_t *d_rects, int nrects, uint32_t *d_query,
+                        uint32_t *h_query_out, void *stream, void *copy_stream);
+
+/* Synchronise the stream, then read and clear the plan's device status word
+ * into *device_status (IHIST_OK if no device error was latched since the
+ * last read).  Returns IHIST_OK or a host/CUDA error code. */
+int ihist_status(ihist_plan_t plan, void *stream, int *device_status);
+
+/* Release the plan and its workspace (NULL is a no-op).  The caller must
+ * make sure no work using the plan is still running. */
+void ihist_destroy(ihist_plan_t plan);
+
+/* Static description of a status code. */
+const char *ihist_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IHIST_H */

@@ -1,0 +1,48 @@
+// ihist_query.cuh -- region histograms by Eq. 2 of arXiv 1711.01919:
+//   h(R, b) = H[y1][x1] - H[y0-1][x1] - H[y1][x0-1] + H[y0-1][x0-1]
+// for inclusive rectangles, terms at index -1 being zero.  Four lookups per
+// (rectangle, bin), independent of the rectangle's area (the O(1) query of
+// Sec. 1).  Evaluated in uint32 modular arithmetic: the true count lies in
+// [0, area], so wrap-around in the intermediate sums cancels exactly.
+#pragma once
+
+#include "ihist_device.cuh"
+
+namespace ihist {
+
+// One thread per (rectangle, bin) pair p = r * B + b, grid-stride.  Output
+// row r of [n][B] is written by B consecutive threads (coalesced).  The
+// rectangle's four ints are re-read by its B threads and served by L1.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256) query_kernel(const uint32_t *__restrict__ hist, int H,
+                                                     int W, int B,
+                                                     const int32_t *__restrict__ rects,
+                                                     unsigned int total,
+                                                     uint32_t *__restrict__ out, Ctrl *ctrl) {
+  const size_t plane = (size_t)H * (size_t)W;
+  for (unsigned int p = blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += gridDim.x * blockDim.x) {
+    const unsigned int r = p / (unsigned)B;
+    const int b = (int)(p - r * (unsigned)B);
+    const int x0 = __ldg(rects + 4 * (size_t)r + 0), y0 = __ldg(rects + 4 * (size_t)r + 1);
+    const int x1 = __ldg(rects + 4 * (size_t)r + 2), y1 = __ldg(rects + 4 * (size_t)r + 3);
+    const bool ok = (0 <= x0) & (x0 <= x1) & (x1 < W) & (0 <= y0) & (y0 <= y1) & (y1 < H);
+    uint32_t v = 0u;
+    if (ok) {
+      // element offset of H at (row y, column x) for this bin
+      auto at = [&](int y, int x) -> size_t {
+        return LAYOUT == 0 ? (size_t)b * plane + (size_t)y * W + x
+                           : ((size_t)y * W + x) * (size_t)B + b;
+      };
+      v = __ldg(hist + at(y1, x1));
+      if (y0 > 0) v -= __ldg(hist + at(y0 - 1, x1));
+      if (x0 > 0) v -= __ldg(hist + at(y1, x0 - 1));
+      if (x0 > 0 && y0 > 0) v += __ldg(hist + at(y0 - 1, x0 - 1));
+    } else if (b == 0) {
+      latch_status(ctrl, kStatusBadRect);
+    }
+    out[p] = v;
+  }
+}
+
+}  // namespace ihist

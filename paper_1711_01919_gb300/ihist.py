@@ -1,0 +1,254 @@
+"""Thin ctypes binding of libihist.so (declared in include/ihist.h).
+
+The functions named ``ihist_*`` mirror the C entry points one to one and only
+marshal arguments: device pointers and streams are plain integers (for torch
+tensors, ``t.data_ptr()`` and ``torch.cuda.current_stream().cuda_stream``).
+Non-zero return codes raise :class:`IhistError`.  ``Plan`` adds the torch
+plumbing (output allocation, stream lookup) around the same calls.
+
+There is no fallback: if libihist.so is missing the import of this module
+succeeds but the first call raises, naming the build step.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libihist.so")
+
+IHIST_OK = 0
+IHIST_ERR_INVALID_ARG = 1
+IHIST_ERR_UNSUPPORTED = 2
+IHIST_ERR_OOM = 3
+IHIST_ERR_CUDA = 4
+IHIST_ERR_LOOKBACK_TIMEOUT = 5
+IHIST_ERR_BAD_RECT = 6
+IHIST_BIN_MAJOR = 0
+IHIST_PIXEL_MAJOR = 1
+
+EXPORTED = (
+    "ihist_plan", "ihist_plan_tuned", "ihist_plan_get_tune", "ihist_workspace_bytes",
+    "ihist_output_bytes", "ihist_compute", "ihist_query", "ihist_sequence_host", "ihist_status",
+    "ihist_destroy", "ihist_error_string",
+)
+
+
+class IhistError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s failed: %s (code %d)" % (what, ihist_error_string(code), code))
+        self.code = code
+
+
+class ihist_tune_t(ctypes.Structure):
+    _fields_ = [
+        ("rows_per_band", ctypes.c_int),
+        ("bins_per_cta", ctypes.c_int),
+        ("chunks_per_warp", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+        ("timeout_us", ctypes.c_uint),
+        ("fault_skip_band", ctypes.c_int),
+        ("reserved", ctypes.c_int * 4),
+    ]
+
+
+TUNE_FIELDS = ("rows_per_band", "bins_per_cta", "chunks_per_warp", "ctas_per_sm", "timeout_us",
+               "fault_skip_band")
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libihist.so and declare its signatures (once)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError("libihist.so is not built (%s); run __graft_entry__.build() or "
+                               "python -m paper_1711_01919_gb300.build" % path)
+        L = ctypes.CDLL(path)
+        vp, sz, ci, cu = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint
+        L.ihist_plan.argtypes = [ci, ci, ci, ci, ctypes.POINTER(vp)]
+        L.ihist_plan.restype = ci
+        L.ihist_plan_tuned.argtypes = [ci, ci, ci, ci, ctypes.POINTER(ihist_tune_t), ctypes.POINTER(vp)]
+        L.ihist_plan_tuned.restype = ci
+        L.ihist_plan_get_tune.argtypes = [vp, ctypes.POINTER(ihist_tune_t)]
+        L.ihist_plan_get_tune.restype = ci
+        L.ihist_workspace_bytes.argtypes = [vp]
+        L.ihist_workspace_bytes.restype = sz
+        L.ihist_output_bytes.argtypes = [ci, ci, ci]
+        L.ihist_output_bytes.restype = sz
+        L.ihist_compute.argtypes = [vp, vp, sz, vp, vp]
+        L.ihist_compute.restype = ci
+        L.ihist_query.argtypes = [vp, vp, vp, ci, vp, vp]
+        L.ihist_query.restype = ci
+        L.ihist_sequence_host.argtypes = [vp, vp, sz, ci, vp, vp, ci, vp, ci, vp, vp, vp, vp]
+        L.ihist_sequence_host.restype = ci
+        L.ihist_status.argtypes = [vp, vp, ctypes.POINTER(ci)]
+        L.ihist_status.restype = ci
+        L.ihist_destroy.argtypes = [vp]
+        L.ihist_destroy.restype = None
+        L.ihist_error_string.argtypes = [ci]
+        L.ihist_error_string.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(code: int, what: str) -> None:
+    if code != IHIST_OK:
+        raise IhistError(code, what)
+
+
+def ihist_error_string(code: int) -> str:
+    return load().ihist_error_string(int(code)).decode()
+
+
+def ihist_output_bytes(h: int, w: int, nbins: int) -> int:
+    return int(load().ihist_output_bytes(h, w, nbins))
+
+
+def _tune_struct(tune) -> ihist_tune_t:
+    t = ihist_tune_t()
+    t.fault_skip_band = -1
+    for k, v in (tune or {}).items():
+        if k not in TUNE_FIELDS:
+            raise KeyError("unknown tuning field %r" % k)
+        setattr(t, k, int(v))
+    return t
+
+
+def ihist_plan(h: int, w: int, nbins: int, layout: int = IHIST_BIN_MAJOR) -> int:
+    out = ctypes.c_void_p()
+    _check(load().ihist_plan(h, w, nbins, layout, ctypes.byref(out)), "ihist_plan")
+    return out.value
+
+
+def ihist_plan_tuned(h: int, w: int, nbins: int, layout: int = IHIST_BIN_MAJOR, tune=None) -> int:
+    out = ctypes.c_void_p()
+    t = _tune_struct(tune)
+    _check(load().ihist_plan_tuned(h, w, nbins, layout, ctypes.byref(t), ctypes.byref(out)),
+           "ihist_plan_tuned")
+    return out.value
+
+
+def ihist_plan_get_tune(plan: int) -> dict:
+    t = ihist_tune_t()
+    _check(load().ihist_plan_get_tune(plan, ctypes.byref(t)), "ihist_plan_get_tune")
+    return {k: getattr(t, k) for k in TUNE_FIELDS}
+
+
+def ihist_workspace_bytes(plan: int) -> int:
+    return int(load().ihist_workspace_bytes(plan))
+
+
+def ihist_compute(plan: int, d_in: int, in_pitch: int, d_out: int, stream: int = 0) -> None:
+    _check(load().ihist_compute(plan, d_in, in_pitch, d_out, stream), "ihist_compute")
+
+
+def ihist_query(plan: int, d_hist: int, d_rects: int, n: int, d_hist_out: int, stream: int = 0) -> None:
+    _check(load().ihist_query(plan, d_hist, d_rects, n, d_hist_out, stream), "ihist_query")
+
+
+def ihist_sequence_host(plan: int, h_frames: int, frame_stride: int, nframes: int, d_slots: int,
+                        d_outs: int, nouts: int, d_rects: int, nrects: int, d_query: int,
+                        h_query_out: int, stream: int, copy_stream: int) -> None:
+    _check(load().ihist_sequence_host(plan, h_frames, frame_stride, nframes, d_slots, d_outs, nouts,
+                                      d_rects, nrects, d_query, h_query_out, stream, copy_stream),
+           "ihist_sequence_host")
+
+
+def ihist_status(plan: int, stream: int = 0) -> int:
+    st = ctypes.c_int(-1)
+    _check(load().ihist_status(plan, stream, ctypes.byref(st)), "ihist_status")
+    return st.value
+
+
+def ihist_destroy(plan: int) -> None:
+    if plan:
+        load().ihist_destroy(plan)
+
+
+# --------------------------------------------------------------- torch glue
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """A plan for (h, w, nbins, layout) frames; torch tensors in and out.
+
+    Output tensors are int32 storage holding uint32 counts (view them as
+    uint32 on the host: ``t.cpu().numpy().view(numpy.uint32)``).
+    """
+
+    def __init__(self, h: int, w: int, nbins: int, layout: int = IHIST_BIN_MAJOR, tune=None):
+        self.h, self.w, self.nbins, self.layout = h, w, nbins, layout
+        self.handle = (ihist_plan_tuned(h, w, nbins, layout, tune) if tune
+                       else ihist_plan(h, w, nbins, layout))
+        self.tune = ihist_plan_get_tune(self.handle)
+
+    @property
+    def out_shape(self):
+        if self.layout == IHIST_BIN_MAJOR:
+            return (self.nbins, self.h, self.w)
+        return (self.h, self.w, self.nbins)
+
+    def empty_output(self, device=None):
+        import torch
+        return torch.empty(self.out_shape, dtype=torch.int32, device=device or "cuda")
+
+    def compute(self, frame, out=None, stream=None):
+        """Integral histogram of a CUDA uint8 [h][w] tensor (row stride may exceed w)."""
+        import torch
+        if frame.dtype != torch.uint8 or frame.dim() != 2 or not frame.is_cuda:
+            raise ValueError("frame must be a 2-D uint8 CUDA tensor")
+        if tuple(frame.shape) != (self.h, self.w) or frame.stride(1) != 1:
+            raise ValueError("frame shape/stride mismatch: %s %s" % (tuple(frame.shape), frame.stride()))
+        if out is None:
+            out = self.empty_output(frame.device)
+        if out.dtype not in (torch.int32,) or not out.is_contiguous() or out.numel() != self.h * self.w * self.nbins:
+            raise ValueError("out must be a contiguous int32 tensor of %d elements" % (self.h * self.w * self.nbins))
+        ihist_compute(self.handle, frame.data_ptr(), frame.stride(0), out.data_ptr(), _stream(stream))
+        return out
+
+    def query(self, hist, rects, out=None, stream=None):
+        """Region histograms (Eq. 2) of CUDA int32 rects [n][4] -> int32 [n][nbins]."""
+        import torch
+        if rects.dtype != torch.int32 or not rects.is_contiguous() or rects.dim() != 2 or rects.shape[1] != 4:
+            raise ValueError("rects must be a contiguous int32 [n][4] tensor")
+        n = rects.shape[0]
+        if out is None:
+            out = torch.empty((n, self.nbins), dtype=torch.int32, device=rects.device)
+        ihist_query(self.handle, hist.data_ptr(), rects.data_ptr(), n, out.data_ptr(), _stream(stream))
+        return out
+
+    def status(self, stream=None) -> int:
+        return ihist_status(self.handle, _stream(stream))
+
+    def workspace_bytes(self) -> int:
+        return ihist_workspace_bytes(self.handle)
+
+    def close(self):
+        if self.handle:
+            ihist_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

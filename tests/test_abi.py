@@ -1,0 +1,80 @@
+"""The C ABI library loads and exports every entry point its header declares
+(no GPU needed; no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1711_01919_gb300 import build as cuda_build
+from paper_1711_01919_gb300 import ihist
+
+HEADER = os.path.join(cuda_build.ROOT, "include", "ihist.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cuda_build.build()
+    return ihist.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ihist_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_binding_names():
+    assert set(declared_functions()) == set(ihist.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(cuda_build.LIB)
+    for name in declared_functions():
+        assert hasattr(so, name), name
+
+
+def test_output_bytes_and_error_strings(lib):
+    assert ihist.ihist_output_bytes(1080, 1920, 64) == 530841600
+    assert ihist.ihist_output_bytes(8192, 8192, 128) == 34359738368
+    assert ihist.ihist_output_bytes(0, 5, 5) == 0
+    for code in range(7):
+        assert ihist.ihist_error_string(code) and ihist.ihist_error_string(code) != "unknown status"
+    assert ihist.ihist_error_string(99) == "unknown status"
+
+
+@pytest.mark.parametrize("h,w,b,layout", [(0, 10, 4, 0), (10, 0, 4, 0), (65536, 4, 4, 0), (4, 4, 0, 0),
+                                          (4, 4, 257, 0), (4, 4, 4, 2), (70000, 70000, 4, 0)])
+def test_plan_rejects_bad_shapes_before_touching_cuda(lib, h, w, b, layout):
+    with pytest.raises(ihist.IhistError) as e:
+        ihist.ihist_plan(h, w, b, layout)
+    assert e.value.code == ihist.IHIST_ERR_INVALID_ARG
+
+
+def test_plan_rejects_bad_tuning(lib):
+    for tune in ({"rows_per_band": 256}, {"bins_per_cta": 5}, {"chunks_per_warp": 3}):
+        with pytest.raises(ihist.IhistError) as e:
+            ihist.ihist_plan_tuned(16, 16, 4, 0, tune)
+        assert e.value.code == ihist.IHIST_ERR_INVALID_ARG
+    with pytest.raises(ihist.IhistError) as e:
+        ihist.ihist_plan(16, 20000, 4, 0)
+    assert e.value.code == ihist.IHIST_ERR_UNSUPPORTED
+
+
+def test_null_plan_calls_are_rejected(lib):
+    L = lib
+    assert L.ihist_compute(None, None, 0, None, None) == ihist.IHIST_ERR_INVALID_ARG
+    assert L.ihist_query(None, None, None, 0, None, None) == ihist.IHIST_ERR_INVALID_ARG
+    st = ctypes.c_int()
+    assert L.ihist_status(None, None, ctypes.byref(st)) == ihist.IHIST_ERR_INVALID_ARG
+    assert L.ihist_workspace_bytes(None) == 0
+    L.ihist_destroy(None)
+
+
+def test_plan_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(ihist.IhistError) as e:
+        ihist.ihist_plan(64, 64, 8, 0)
+    assert e.value.code == ihist.IHIST_ERR_CUDA
