@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Benchmark: integral histograms of a 64-frame 1920x1080 sequence, 64 bins.
+
+One step = one pass of the hot path over the 64 frames: the fused quantise +
+2-D scan (rows a1-a5) of every frame in one persistent batched launch, and a
+region query of 1000 rectangles per frame (row a6) in one launch.  ``value``
+is frames/s with the frames already resident in HBM; the plain per-frame
+form (64 launches of each kernel) is reported beside it.  ``e2e`` is the same
+metric through ``ihist_batch_upload_compute`` (row a7): frames in pinned host
+memory, uploaded on a copy stream, two 32-frame batches alternating so one
+uploads while the other computes, query results copied back to the host --
+all inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank is an independent replica on its own GPU with its
+own frames (the work shards by frame; no collective on the data path); rank 0
+prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IH frames/s & written GB/s vs HBM peak; served p50/p99 vs plain per-frame launch"
+H, W, NBINS, NFRAMES, NRECTS = 1080, 1920, 64, 64, 1000
+SIGMA = 20.0
+WORKLOAD = ("sequence of 64 frames 1920x1080 uint8, smooth gradient + Gaussian noise sigma=20 "
+            "clipped to [0,255], B=64 uniform bins, uint32 bin-major output, 1000 region queries per frame")
+PROFILE = os.path.join(ROOT, "profiles", "batch_kernel_64x1080p_b64.txt")
+SCAN_SOURCES = ("ihist_scan.cuh", "ihist_device.cuh")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--e2e-steps", type=int, default=0, help="0 = min(steps, 30)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=64,
+                    help="frames per step (64 = the workload; smaller only for profiler captures)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def make_frames(rank: int, n: int = 0) -> np.ndarray:
+    from paper_1711_01919_gb300 import synth
+    n = n or NFRAMES
+    seed = synth.workload_seed(2)
+    out = np.empty((n, H, W), dtype=np.uint8)
+    for f in range(n):
+        out[f] = synth.gradient_frame(synth.substream_seed(seed, rank * 100000 + f), H, W, SIGMA)
+    return out
+
+
+def make_rects() -> np.ndarray:
+    from paper_1711_01919_gb300 import synth
+    return synth.rects(synth.workload_seed(2) + 1, NRECTS, H, W)
+
+
+def algorithmic_bytes_per_frame() -> int:
+    return H * W * NBINS * 4 + H * W  # uint32 output written once + uint8 frame read once
+
+
+def scan_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in SCAN_SOURCES:
+        with open(os.path.join(ROOT, "paper_1711_01919_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per scan launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    try:
+        kv = {}
+        for line in open(PROFILE):
+            if "=" in line and not line.lstrip().startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("scan_source_sha256_16") != scan_source_hash():
+            return None
+        return int(float(kv["traffic_bytes_per_launch"]))
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self, bus_id: str | None):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        allrows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 10:
+                allrows.append(parts)
+        rows = [r for r in allrows if bus_id and r[1].lower().endswith(bus_id.lower())]
+        if not rows and len({r[1] for r in allrows}) == 1:
+            rows = allrows
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[6:10]) if v.strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(frames: np.ndarray, seconds: float, threads: int) -> dict:
+    """The CPU oracle (Algorithm 1) on a bounded sample of the frames."""
+    import oracle
+    out = np.empty((NBINS, H, W), dtype=np.uint32)
+    done, t0 = 0, time.perf_counter()
+    while done < len(frames) and (done == 0 or time.perf_counter() - t0 < seconds):
+        if threads > 1:
+            oracle.integral_histogram_threads(frames[done], NBINS, threads, out)
+        else:
+            oracle.integral_histogram(frames[done], NBINS, out)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "frames/s", "cores": threads, "kind": "oracle",
+            "sample": "%d of the %d frames (1920x1080, 64 bins), %s Algorithm 1 in C, %.1f s"
+                      % (done, len(frames), "bins-parallel" if threads > 1 else "single-threaded", dt)}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    frames = make_frames(0, max(1, min(NFRAMES, args.steps + args.warmup)))
+    cores = host_cores()
+    out = np.empty((NBINS, H, W), dtype=np.uint32)
+    for i in range(args.warmup):
+        oracle.integral_histogram_threads(frames[i % len(frames)], NBINS, cores, out)
+    times = []
+    used = cores
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        _, used = oracle.integral_histogram_threads(frames[(args.warmup + i) % len(frames)], NBINS, cores, out)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_step": 1, "H": H, "W": W, "B": NBINS,
+                   "layout": "bin-major", "step": "one frame (bounded sample of the 64-frame sequence)"},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": used, "kind": "oracle",
+                         "sample": "%d frames of the workload, one per step, bins-parallel Algorithm 1 in C"
+                                   % args.steps},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    global NFRAMES
+    args = parse_args()
+    if args.frames != NFRAMES:
+        if args.frames < 2 or args.frames % 2:
+            raise SystemExit("--frames must be an even number >= 2")
+        NFRAMES = args.frames
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_1711_01919_gb300 import build as cuda_build
+    from paper_1711_01919_gb300 import ihist
+
+    rank, world, local_rank = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or not os.path.exists(cuda_build.LIB):
+        cuda_build.build()
+    if world > 1:
+        dist.barrier()
+    ihist.load()
+
+    frames = make_frames(rank)
+    rects = make_rects()
+    d_frames = torch.from_numpy(frames).to(dev)
+    # every frame queries the same rectangles: [frames][rects][4]
+    d_rects = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(rects, (NFRAMES,) + rects.shape))).to(dev)
+    outs = torch.empty((NFRAMES, NBINS, H, W), dtype=torch.int32, device=dev)
+    d_query = torch.empty((NFRAMES * NRECTS * NBINS,), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+
+    # the batched form: one persistent launch over all 64 resident frames,
+    # one launch for all 64 x 1000 region queries
+    batch = ihist.Batch([d_frames[f] for f in range(NFRAMES)], NBINS, outs=[outs[f] for f in range(NFRAMES)])
+    rp, qp = d_rects.data_ptr(), d_query.data_ptr()
+
+    def step():
+        ihist.ihist_batch_compute(batch.handle, s)
+        ihist.ihist_batch_query_all(batch.handle, rp, NRECTS, qp, s)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if batch.status() != ihist.IHIST_OK:
+        raise SystemExit("device status error during warm-up")
+
+    # ---- device-resident timed region ----
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler()
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(args.steps):
+        kev[k][0].record(stream)
+        ihist.ihist_batch_compute(batch.handle, s)
+        kev[k][1].record(stream)
+        ihist.ihist_batch_query_all(batch.handle, rp, NRECTS, qp, s)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        bus = "%02x:%02x.0" % (props.pci_bus_id, props.pci_device_id)
+    except AttributeError:
+        bus = None
+    clk = clocks.stop(bus)
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kernel_ms = [a.elapsed_time(b) for a, b in kev]
+    if batch.status() != ihist.IHIST_OK:
+        raise SystemExit("device status error during the timed region")
+    resident_query = d_query.view(NFRAMES, NRECTS, NBINS)[NFRAMES - 1].cpu()
+
+    # ---- plain per-frame launches (same frames, same outputs) ----
+    plan = ihist.Plan(H, W, NBINS, ihist.IHIST_BIN_MAJOR)
+    pf_steps = max(3, min(args.steps, 20))
+
+    def plain_step():
+        for f in range(NFRAMES):
+            ihist.ihist_compute(plan.handle, d_frames[f].data_ptr(), W, outs[f].data_ptr(), s)
+            ihist.ihist_query(plan.handle, outs[f].data_ptr(), rp, NRECTS, d_query[f * NRECTS * NBINS:].data_ptr(), s)
+
+    for _ in range(2):
+        plain_step()
+    p_start, p_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    p_start.record(stream)
+    for _ in range(pf_steps):
+        plain_step()
+    p_end.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p_start.elapsed_time(p_end)
+    if plan.status() != ihist.IHIST_OK:
+        raise SystemExit("device status error in the per-frame run")
+    if not torch.equal(d_query.view(NFRAMES, NRECTS, NBINS)[NFRAMES - 1].cpu(), resident_query):
+        raise SystemExit("per-frame and batched query results differ")
+
+    # ---- end-to-end: pinned host frames -> copy stream -> batched compute ->
+    # batched query -> host; two 32-frame batches alternate so one batch's
+    # upload overlaps the other's compute ----
+    e2e_steps = args.e2e_steps or min(args.steps, 30)
+    half = NFRAMES // 2
+    h_frames = torch.from_numpy(frames).pin_memory()
+    h_query = torch.empty((NFRAMES * NRECTS * NBINS,), dtype=torch.int32).pin_memory()
+    d_in2 = torch.empty((NFRAMES, H, W), dtype=torch.uint8, device=dev)
+    halves = [ihist.Batch([d_in2[f] for f in range(g * half, (g + 1) * half)], NBINS,
+                          outs=[outs[f] for f in range(g * half, (g + 1) * half)]) for g in range(2)]
+    copy_stream = torch.cuda.Stream(dev)
+    hq = [h_frames[f] for f in range(NFRAMES)]
+    qsz = half * NRECTS * NBINS
+
+    def e2e_step():
+        for g in range(2):
+            ihist.ihist_batch_upload_compute(halves[g].handle, [x.data_ptr() for x in hq[g * half:(g + 1) * half]],
+                                             s, copy_stream.cuda_stream)
+            ihist.ihist_batch_query_all(halves[g].handle, d_rects[g * half:].data_ptr(), NRECTS,
+                                        d_query[g * qsz:].data_ptr(), s)
+        h_query.copy_(d_query, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e_start.record(stream)
+    copy_stream.wait_event(e_start)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e_start.elapsed_time(e_end)
+    for hb in halves:
+        if hb.status() != ihist.IHIST_OK:
+            raise SystemExit("device status error during the e2e region")
+    if not torch.equal(h_query.view(NFRAMES, NRECTS, NBINS)[NFRAMES - 1], resident_query):
+        raise SystemExit("e2e query results differ from the device-resident run")
+
+    times = torch.tensor([elapsed_ms, e2e_ms, plain_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    elapsed_ms, e2e_ms, plain_ms = times.tolist()
+
+    if rank == 0:
+        frames_total = world * NFRAMES * args.steps
+        value = frames_total / (elapsed_ms / 1000.0)
+        peak, peak_kind = measured_peak()
+        bytes_per_launch = NFRAMES * algorithmic_bytes_per_frame()
+        mean_kernel_s = statistics.fmean(kernel_ms) / 1000.0
+        achieved = bytes_per_launch / mean_kernel_s / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {
+                "workload": WORKLOAD, "frames_per_step": NFRAMES, "H": H, "W": W, "B": NBINS,
+                "layout": "bin-major", "queries_per_frame": NRECTS,
+                "form": "batched: one persistent scan launch over the %d resident frames + one query launch" % NFRAMES,
+                "parallelism": "replicas (one independent 64-frame sequence per GPU)" if world > 1 else "single GPU",
+                "l2": "no flush: each step writes %.1f GB of output, > 129 MB L2" % (NFRAMES * H * W * NBINS * 4 / 1e9),
+                "written_gbs": world * NFRAMES * args.steps * H * W * NBINS * 4 / (elapsed_ms / 1000.0) / 1e9,
+                "batch_items_per_launch": batch.items(),
+                "scan_launch_ms_median": statistics.median(kernel_ms),
+                "plain_per_frame": {
+                    "value": world * NFRAMES * pf_steps / (plain_ms / 1000.0), "unit": "frames/s",
+                    "steps": pf_steps, "form": "%d x (ihist_compute + ihist_query) per step" % NFRAMES,
+                    "tile": plan.tune},
+            },
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_traffic(),
+                         "kernel": "ihist::batch_kernel (%d frames per launch)" % NFRAMES,
+                         "bytes_per_launch": bytes_per_launch,
+                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind},
+            "e2e": {"value": world * NFRAMES * e2e_steps / (e2e_ms / 1000.0), "unit": "frames/s",
+                    "h2d_bytes_per_step": NFRAMES * H * W, "d2h_bytes_per_step": NFRAMES * NRECTS * NBINS * 4,
+                    "steps": e2e_steps,
+                    "api": "ihist_batch_upload_compute on two alternating %d-frame batches (pinned host frames, "
+                           % (NFRAMES // 2) +
+                           "copy stream) + ihist_batch_query_all + copy of the query results to pinned host"},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            line["cpu_baseline"] = cpu_baseline(frames, args.cpu_seconds, 1)
+            line["cpu_baseline_all_cores"] = cpu_baseline(frames, args.cpu_seconds / 2, host_cores())
+        print(json.dumps(line), flush=True)
+    for hb in halves:
+        hb.close()
+    batch.close()
+    plan.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -63,10 +63,13 @@ typedef struct ihist_plan_s *ihist_plan_t;
 /* Tile shape of the fused scan kernel.  Zero fields take the library's
  * default for the frame shape.
  *   rows_per_band   R, rows one CTA owns (1..255)
- *   bins_per_cta    G, bins one CTA owns (4, 8 or 16)
+ *   bins_per_cta    G, bins one CTA owns (4, 8 or 16; default 4)
  *   chunks_per_warp m, 128-column chunks one warp owns (1, 2, 4 or 8;
- *                   at most 2 with bins_per_cta 16);
- *                   the CTA has ceil(ceil(w/128)/m) warps (at most 16)
+ *                   at most 2 with bins_per_cta 16)
+ *   groups_per_cta  bin groups one CTA serves side by side (warps = groups
+ *                   x ceil(ceil(w/128)/m), at most 16 in all); narrow frames
+ *                   fill a CTA this way
+ *   ctas_per_sm     persistent grid = ctas_per_sm x SMs (0 = occupancy limit)
  *   timeout_us      limit of each carry wait before it gives up and latches
  *                   IHIST_ERR_LOOKBACK_TIMEOUT (default 2,000,000 us)
  *   fault_skip_band test hook, -1 = off: the CTAs of this band publish no
@@ -76,10 +79,11 @@ typedef struct {
   int rows_per_band;
   int bins_per_cta;
   int chunks_per_warp;
-  int ctas_per_sm;   /* persistent grid = ctas_per_sm x SMs (0 = occupancy limit) */
+  int ctas_per_sm;
   unsigned int timeout_us;
   int fault_skip_band;
-  int reserved[4];
+  int groups_per_cta;
+  int reserved[3];
 } ihist_tune_t;
 
 /* Create a plan for frames of h rows x w columns and nbins bins in the given
@@ -138,6 +142,75 @@ int ihist_sequence_host(ihist_plan_t plan, const uint8_t *h_frames, size_t frame
                         int nframes, uint8_t *d_slots, uint32_t *d_outs, int nouts,
                         const int32_t *d_rects, int nrects, uint32_t *d_query,
                         uint32_t *h_query_out, void *stream, void *copy_stream);
+
+/* ---- Batches: many frames of uneven size in one persistent launch -------
+ *
+ * A batch is a work-list over several frames (any mix of shapes, bin counts
+ * and layouts): one launch computes every frame's integral histogram, so the
+ * ramp and tail of a launch are paid once per batch instead of once per
+ * frame.  The same fused kernel runs on each frame (Eq. 1; Sec. 4.4's image
+ * sequences as one launch), and results equal ihist_compute's word for word.
+ * The launch needs no host-side reset between calls, so it can be captured
+ * in a CUDA graph and replayed. */
+typedef struct ihist_batch_s *ihist_batch_t;
+
+/* One frame of a batch.  d_in: h rows of w bytes, row stride in_pitch;
+ * d_out: ihist_output_bytes(h, w, nbins) bytes in `layout`.  Both are device
+ * pointers the caller owns and keeps valid while the batch may run. */
+typedef struct {
+  int h, w, nbins, layout;
+  const uint8_t *d_in;
+  size_t in_pitch;
+  uint32_t *d_out;
+} ihist_frame_t;
+
+/* Plan a batch of n >= 1 frames (limits per frame as for ihist_plan).  tune
+ * may be NULL; its bins_per_cta (4 or 8) and rows_per_band apply to every
+ * frame, chunks_per_warp and groups_per_cta are chosen per frame to fill
+ * a CTA of up to 16 warps.  Allocates the batch's device workspace. */
+int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_tune_t *tune,
+                     ihist_batch_t *out);
+
+/* Point the batch's frames at new buffers (shapes, bin counts and layouts
+ * must equal the planned ones).  The new descriptors are copied on `stream`,
+ * so later launches on that stream see them. */
+int ihist_batch_set_io(ihist_batch_t batch, const ihist_frame_t *frames, int n, void *stream);
+
+/* Compute every frame of the batch in one launch on `stream`. */
+int ihist_batch_compute(ihist_batch_t batch, void *stream);
+
+/* Region histograms (Eq. 2) on frame `frame` of the batch; arguments as for
+ * ihist_query. */
+int ihist_batch_query(ihist_batch_t batch, int frame, const uint32_t *d_hist,
+                      const int32_t *d_rects, int n, uint32_t *d_hist_out, void *stream);
+
+/* Region histograms (Eq. 2) on every frame of the batch in one launch.
+ * d_rects: nframes x n rectangles ({x0, y0, x1, y1} int32, inclusive),
+ * frame f's at d_rects + 4*n*f.  d_out: frame f's n x nbins_f rows start
+ * after those of frames 0..f-1 (offset n * sum of their bin counts words).
+ * Out-of-range rectangles give zero rows and latch IHIST_ERR_BAD_RECT. */
+int ihist_batch_query_all(ihist_batch_t batch, const int32_t *d_rects, int n, uint32_t *d_out,
+                          void *stream);
+
+/* Upload every frame of the batch from page-locked HOST memory on
+ * copy_stream (h_frames[i]: h x w bytes, rows packed) into the batch's
+ * device inputs, then compute the batch on `stream` once the copies land
+ * (Algorithm 6's dual buffering, one batch at a time).  Two batches driven
+ * alternately overlap one batch's upload with the other's compute.  The
+ * copies of a call wait for this batch's previous compute, so inputs are
+ * never overwritten while still being read. */
+int ihist_batch_upload_compute(ihist_batch_t batch, const uint8_t *const *h_frames, void *stream,
+                               void *copy_stream);
+
+/* As ihist_status, for the batch's status word. */
+int ihist_batch_status(ihist_batch_t batch, void *stream, int *device_status);
+
+/* Device workspace bytes the batch holds; number of work items per launch. */
+size_t ihist_batch_workspace_bytes(ihist_batch_t batch);
+unsigned int ihist_batch_items(ihist_batch_t batch);
+
+/* Release the batch (NULL is a no-op); no launch of it may still be running. */
+void ihist_batch_destroy(ihist_batch_t batch);
 
 /* Synchronise the stream, then read and clear the plan's device status word
  * into *device_status (IHIST_OK if no device error was latched since the

@@ -106,11 +106,14 @@ class Oracle:
         """Q of Eq. 1 for one intensity value."""
         return int(self.lib.oracle_bin_of(int(v), int(nbins)))
 
-    def integral_histogram(self, img, nbins: int) -> np.ndarray:
+    def integral_histogram(self, img, nbins: int, out=None) -> np.ndarray:
         """Algorithm 1: the [nbins][h][w] uint32 integral histogram of img."""
         a = _img(img)
         h, w = a.shape
-        out = np.empty((nbins, h, w), dtype=np.uint32)
+        if out is None:
+            out = np.empty((nbins, h, w), dtype=np.uint32)
+        if out.shape != (nbins, h, w) or out.dtype != np.uint32 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous uint32 [nbins][h][w] array")
         if h and w and nbins:
             self.lib.oracle_ih(_p8(a), a.strides[0], h, w, nbins, _p32(out))
         return out
@@ -169,8 +172,8 @@ def bin_of(v, nbins):
     return default().bin_of(v, nbins)
 
 
-def integral_histogram(img, nbins):
-    return default().integral_histogram(img, nbins)
+def integral_histogram(img, nbins, out=None):
+    return default().integral_histogram(img, nbins, out)
 
 
 def integral_histogram_plane(img, nbins, k, out=None):

@@ -1,6 +1,8 @@
 // ihist_api.cu -- host side of libihist.so: argument validation, plan and
 // workspace management, kernel selection and launches.  Declared in
 // include/ihist.h.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -8,45 +10,34 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <vector>
 
-#include "../../include/ihist.h"
+#include "ihist.h"
+#include "ihist_kernels.h"
 #include "ihist_query.cuh"
-#include "ihist_scan.cuh"
 
 using namespace ihist;
 
 namespace {
 
-using ScanFn = void (*)(FrameDesc, Ctrl *, unsigned long long);
-
-template <int G, int MMAX>
-ScanFn pick_vec(bool vec) {
-  return vec ? scan_kernel<G, MMAX, true> : scan_kernel<G, MMAX, false>;
-}
-
-template <int G>
-ScanFn pick_m(int mmax, bool vec) {
-  switch (mmax) {
-    case 1: return pick_vec<G, 1>(vec);
-    case 2: return pick_vec<G, 2>(vec);
-    case 4: return pick_vec<G, 4>(vec);
-    default: return pick_vec<G, 8>(vec);
-  }
-}
-
-// G = 16 keeps 64 accumulators per lane; it is built for up to 2 chunks per warp only.
-ScanFn pick_scan(int G, int mmax, bool vec) {
-  switch (G) {
-    case 4: return pick_m<4>(mmax, vec);
-    case 8: return pick_m<8>(mmax, vec);
-    default:
-      if (mmax == 1) return pick_vec<16, 1>(vec);
-      if (mmax == 2) return pick_vec<16, 2>(vec);
-      return nullptr;
-  }
-}
-
 int mmax_for(int m) { return m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : 8; }
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependency on libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
 
 constexpr unsigned int kDefaultTimeoutUs = 2000000u;
 
@@ -58,7 +49,7 @@ struct ihist_plan_s {
   int device;
   int sms;
   int H, W, B, layout;
-  int R, G, m, NW, nbands, ngroups, nchunks;
+  int R, G, m, NW, nbands, ngroups, nchunks, wpg, gpc, ngsets;
   unsigned int nitems;
   int ctas_per_sm;
   unsigned int timeout_us;
@@ -70,6 +61,13 @@ struct ihist_plan_s {
   uint32_t *flags, *agg_cnt, *agg_left, *incl;
   cudaEvent_t ev_uploaded[2];  // sequence pipeline: slot filled
   cudaEvent_t ev_consumed[2];  // sequence pipeline: slot read by its compute
+  struct {
+    const void *ptr;
+    size_t pitch;
+    bool ok;
+    CUtensorMap map;
+  } tmaps[4];                  // TMA descriptors of recent inputs (round robin)
+  int tmap_next;
 };
 
 extern "C" size_t ihist_output_bytes(int h, int w, int nbins) {
@@ -99,21 +97,81 @@ static int validate_shape(int h, int w, int nbins, int layout) {
   return IHIST_OK;
 }
 
-// Default tiling: G = 8 bins per CTA (4 for B < 8); m so that the CTA has at
-// most 16 warps for w <= 8192; R so that bands x groups gives about two work
-// items per SM.
-static void default_tune(int h, int w, int nbins, int sms, ihist_tune_t *t) {
-  const int nchunks = (w + kChunk - 1) / kChunk;
-  if (t->bins_per_cta == 0) t->bins_per_cta = nbins >= 8 ? 8 : 4;
-  if (t->chunks_per_warp == 0)
-    t->chunks_per_warp = nchunks <= 16 ? 1 : nchunks <= 32 ? 2 : nchunks <= 64 ? 4 : 8;
-  if (t->rows_per_band == 0) {
-    const int ngroups = (nbins + t->bins_per_cta - 1) / t->bins_per_cta;
-    long long r = (long long)h * ngroups / (2LL * sms);
-    r = std::max(8LL, std::min(128LL, r));
-    t->rows_per_band = (int)std::min<long long>(r, h);
+// Largest dynamic shared memory a CTA may opt into, set once on every
+// instantiation a plan may launch so that occupancy queries and launches
+// can use any tile size up to it.
+static int prepare_kernels(int G, int mmax, int dev, size_t *optin) {
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return IHIST_ERR_CUDA;
+  size_t dyn = (size_t)v;
+  for (int tma = 0; tma < 2; ++tma)
+    for (int vec = 0; vec < 2; ++vec) {
+      ScanFn fn = scan_fn(G, mmax, tma != 0, vec != 0);
+      if (!fn) return IHIST_ERR_UNSUPPORTED;
+      cudaFuncAttributes a;
+      if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return IHIST_ERR_CUDA;
+      }
+      // dynamic + static shared memory must fit the opt-in limit
+      const size_t d = (size_t)v > a.sharedSizeBytes ? (size_t)v - a.sharedSizeBytes : 0;
+      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d) != cudaSuccess) {
+        cudaGetLastError();
+        return IHIST_ERR_CUDA;
+      }
+      dyn = std::min(dyn, d);
+    }
+  *optin = dyn;
+  return IHIST_OK;
+}
+
+static int occupancy(ScanFn fn, int threads, size_t smem) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
   }
-  if (t->timeout_us == 0) t->timeout_us = kDefaultTimeoutUs;
+  return occ;
+}
+
+// Default tiling: the (rows per band R, bin groups per CTA) that maximise
+// (fraction of persistent-CTA slot time the work items fill, counting the
+// last partial wave) x (1 - carry overhead, about 1.25/R of the output
+// bytes) x (warps per SM, up to 24) x (fraction of CTA bin groups in use).
+// Fields the caller fixed (non-zero) are kept.
+static void default_tiling(int h, int ngroups, int wpg, int G, int nchunks, int sms, ScanFn fn,
+                           size_t optin, int *R, int *gpc) {
+  double best = -1.0;
+  int best_r = *R ? *R : std::min(h, 8), best_g = *gpc ? *gpc : 1;
+  const int g_lo = *gpc ? *gpc : 1;
+  const int g_hi = *gpc ? *gpc : std::max(1, std::min(ngroups, 16 / wpg));
+  for (int gp = g_lo; gp <= g_hi; ++gp) {
+    const int NW = gp * wpg;
+    const int ngsets = (ngroups + gp - 1) / gp;
+    const double used = (double)ngroups / (double)(ngsets * gp);
+    const int r_lo = *R ? *R : std::min(h, 8), r_hi = *R ? *R : std::min(h, 255);
+    for (int r = r_lo; r <= r_hi; ++r) {
+      const size_t smem = smem_layout(NW, r, G, nchunks * gp).bytes;
+      if (smem > optin) break;
+      const int occ = occupancy(fn, NW * 32, smem);
+      if (occ < 1) break;
+      const long long slots = (long long)occ * sms;
+      const long long items = (long long)((h + r - 1) / r) * ngsets;
+      const long long waves = (items + slots - 1) / slots;
+      const double fill = (double)items / (double)(waves * slots);
+      const double carry = 1.0 - 1.25 / r;
+      const double warps = std::min(1.0, occ * NW / 24.0);
+      const double score = fill * carry * warps * used;
+      if (score > best) {
+        best = score;
+        best_r = r;
+        best_g = gp;
+      }
+    }
+  }
+  *R = best_r;
+  *gpc = best_g;
 }
 
 extern "C" int ihist_plan_tuned(int h, int w, int nbins, int layout, const ihist_tune_t *tune,
@@ -132,13 +190,31 @@ extern "C" int ihist_plan_tuned(int h, int w, int nbins, int layout, const ihist
       t.chunks_per_warp != 4 && t.chunks_per_warp != 8)
     return IHIST_ERR_INVALID_ARG;
   if (t.ctas_per_sm < 0 || t.ctas_per_sm > 32) return IHIST_ERR_INVALID_ARG;
+  if (t.groups_per_cta < 0 || t.groups_per_cta > 16) return IHIST_ERR_INVALID_ARG;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return IHIST_ERR_CUDA;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return IHIST_ERR_CUDA;
-  default_tune(h, w, nbins, sms, &t);
+  const int nchunks = (w + kChunk - 1) / kChunk;
+  if (t.bins_per_cta == 0) t.bins_per_cta = 4;
+  if (t.chunks_per_warp == 0)
+    t.chunks_per_warp = nchunks <= 16 ? 1 : nchunks <= 32 ? 2 : nchunks <= 64 ? 4 : 8;
+  if (t.timeout_us == 0) t.timeout_us = kDefaultTimeoutUs;
+  const int wpg = (nchunks + t.chunks_per_warp - 1) / t.chunks_per_warp;
+  const int mmax = mmax_for(t.chunks_per_warp);
+  if (wpg * std::max(1, t.groups_per_cta) > 16 || !scan_fn(t.bins_per_cta, mmax, true, true))
+    return IHIST_ERR_UNSUPPORTED;
+  size_t optin = 0;
+  rc = prepare_kernels(t.bins_per_cta, mmax, dev, &optin);
+  if (rc != IHIST_OK) return rc;
+  ScanFn fn = scan_fn(t.bins_per_cta, mmax, true, true);
+  const int ngroups = (nbins + t.bins_per_cta - 1) / t.bins_per_cta;
+  if (t.groups_per_cta > ngroups) t.groups_per_cta = ngroups;
+  if (t.rows_per_band == 0 || t.groups_per_cta == 0)
+    default_tiling(h, ngroups, wpg, t.bins_per_cta, nchunks, sms, fn, optin, &t.rows_per_band,
+                   &t.groups_per_cta);
 
   ihist_plan_s *p = new (std::nothrow) ihist_plan_s;
   if (!p) return IHIST_ERR_OOM;
@@ -152,43 +228,26 @@ extern "C" int ihist_plan_tuned(int h, int w, int nbins, int layout, const ihist
   p->G = t.bins_per_cta;
   p->m = t.chunks_per_warp;
   p->R = std::min(t.rows_per_band, h);
-  p->nchunks = (w + kChunk - 1) / kChunk;
-  p->NW = (p->nchunks + p->m - 1) / p->m;
-  if (p->NW > 16 || !pick_scan(p->G, mmax_for(p->m), true)) {
-    delete p;
-    return IHIST_ERR_UNSUPPORTED;
-  }
+  p->nchunks = nchunks;
+  p->wpg = wpg;
+  p->gpc = t.groups_per_cta;
+  p->NW = wpg * p->gpc;
   p->nbands = (h + p->R - 1) / p->R;
-  p->ngroups = (nbins + p->G - 1) / p->G;
-  p->nitems = (unsigned int)p->nbands * (unsigned int)p->ngroups;
+  p->ngroups = ngroups;
+  p->ngsets = (ngroups + p->gpc - 1) / p->gpc;
+  p->nitems = (unsigned int)p->nbands * (unsigned int)p->ngsets;
   p->timeout_us = t.timeout_us;
   p->fault_skip_band = t.fault_skip_band;
-  p->smem_bytes = ((size_t)p->NW * p->R * p->G + (size_t)p->nchunks * p->G) * sizeof(uint32_t);
-
-  ScanFn fn = pick_scan(p->G, mmax_for(p->m), true);
-  ScanFn fn2 = pick_scan(p->G, mmax_for(p->m), false);
-  if (p->smem_bytes > 48 * 1024) {
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_bytes) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(fn2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)p->smem_bytes) != cudaSuccess) {
-      cudaGetLastError();
-      delete p;
-      return IHIST_ERR_UNSUPPORTED;
-    }
-  }
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->NW * 32, p->smem_bytes) !=
-          cudaSuccess ||
-      occ < 1) {
-    cudaGetLastError();
+  p->smem_bytes = smem_layout(p->NW, p->R, p->G, p->nchunks * p->gpc).bytes;
+  const int occ = p->smem_bytes <= optin ? occupancy(fn, p->NW * 32, p->smem_bytes) : 0;
+  if (occ < 1) {
     delete p;
     return IHIST_ERR_UNSUPPORTED;
   }
   p->ctas_per_sm = t.ctas_per_sm > 0 ? std::min(t.ctas_per_sm, occ) : occ;
 
   // workspace: control block, flags, column-count aggregates, left counts, inclusive rows
-  const size_t nci = (size_t)p->nitems * p->nchunks;
+  const size_t nci = (size_t)p->nbands * p->ngroups * p->nchunks;
   size_t off = 0;
   const size_t o_ctrl = off;
   off = align_up(off + sizeof(Ctrl), 256);
@@ -248,6 +307,7 @@ extern "C" int ihist_plan_get_tune(ihist_plan_t p, ihist_tune_t *out) {
   out->ctas_per_sm = p->ctas_per_sm;
   out->timeout_us = p->timeout_us;
   out->fault_skip_band = p->fault_skip_band;
+  out->groups_per_cta = p->gpc;
   return IHIST_OK;
 }
 
@@ -259,6 +319,31 @@ static int check_device(const ihist_plan_s *p) {
   return dev == p->device ? IHIST_OK : IHIST_ERR_INVALID_ARG;
 }
 
+// TMA descriptor of the input frame: 2-D uint8 tensor {w, h} with row stride
+// `pitch`, box {128 columns, R rows}, zero fill outside the frame.  Needs a
+// 16-byte aligned base and pitch (the tensor-map rules) and w >= 128.
+static const CUtensorMap *input_map(ihist_plan_s *p, const uint8_t *d_in, size_t pitch) {
+  if (((uintptr_t)d_in & 15u) || (pitch & 15u) || p->W < kChunk || pitch >= (1ull << 40))
+    return nullptr;
+  for (auto &e : p->tmaps)
+    if (e.ptr == d_in && e.pitch == pitch) return e.ok ? &e.map : nullptr;
+  auto &e = p->tmaps[p->tmap_next];
+  p->tmap_next = (p->tmap_next + 1) % 4;
+  e.ptr = d_in;
+  e.pitch = pitch;
+  e.ok = false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return nullptr;
+  cuuint64_t gdim[2] = {(cuuint64_t)p->W, (cuuint64_t)p->H};
+  cuuint64_t gstride[1] = {(cuuint64_t)pitch};
+  cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)p->R};
+  cuuint32_t estride[2] = {1u, 1u};
+  e.ok = enc(&e.map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(d_in), gdim, gstride, box,
+             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return e.ok ? &e.map : nullptr;
+}
+
 extern "C" int ihist_compute(ihist_plan_t p, const uint8_t *d_in, size_t in_pitch, uint32_t *d_out,
                              void *stream) {
   if (!p || !d_in || !d_out) return IHIST_ERR_INVALID_ARG;
@@ -266,8 +351,13 @@ extern "C" int ihist_compute(ihist_plan_t p, const uint8_t *d_in, size_t in_pitc
   if (((uintptr_t)d_out & 3u) != 0) return IHIST_ERR_INVALID_ARG;
   int rc = check_device(p);
   if (rc != IHIST_OK) return rc;
-  const bool vec = ((uintptr_t)d_in % 4 == 0) && (in_pitch % 4 == 0) && (p->W % 4 == 0) &&
-                   ((uintptr_t)d_out % 16 == 0);
+  const bool vec = (p->W % 4 == 0) && ((uintptr_t)d_out % 16 == 0);
+  const CUtensorMap *tm = input_map(p, d_in, in_pitch);
+  CUtensorMap tmap;
+  if (tm)
+    tmap = *tm;
+  else
+    std::memset(&tmap, 0, sizeof(tmap));
   FrameDesc f;
   std::memset(&f, 0, sizeof(f));
   f.in = d_in;
@@ -282,6 +372,9 @@ extern "C" int ihist_compute(ihist_plan_t p, const uint8_t *d_in, size_t in_pitc
   f.ngroups = p->ngroups;
   f.nchunks = p->nchunks;
   f.m = p->m;
+  f.wpg = p->wpg;
+  f.gpc = p->gpc;
+  f.ngsets = p->ngsets;
   f.fault_skip_band = p->fault_skip_band;
   f.nitems = p->nitems;
   f.agg_cnt = p->agg_cnt;
@@ -290,9 +383,32 @@ extern "C" int ihist_compute(ihist_plan_t p, const uint8_t *d_in, size_t in_pitc
   f.flags = p->flags;
   const unsigned int grid =
       std::min<unsigned int>(p->nitems, (unsigned int)(p->ctas_per_sm * p->sms));
-  ScanFn fn = pick_scan(p->G, mmax_for(p->m), vec);
+  ScanFn fn = scan_fn(p->G, mmax_for(p->m), tm != nullptr, vec);
   const unsigned long long timeout_ns = (unsigned long long)p->timeout_us * 1000ull;
-  fn<<<grid, p->NW * 32, p->smem_bytes, (cudaStream_t)stream>>>(f, p->ctrl, timeout_ns);
+  fn<<<grid, p->NW * 32, p->smem_bytes, (cudaStream_t)stream>>>(f, tmap, p->ctrl, timeout_ns);
+  if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
+  return IHIST_OK;
+}
+
+// Eq. 2 launch shared by plans and batches.
+static int launch_query(int H, int W, int B, int layout, int sms, Ctrl *ctrl, const uint32_t *d_hist,
+                        const int32_t *d_rects, int n, uint32_t *d_hist_out, void *stream) {
+  if (n < 0) return IHIST_ERR_INVALID_ARG;
+  if (n == 0) return IHIST_OK;
+  if (!d_hist || !d_rects || !d_hist_out) return IHIST_ERR_INVALID_ARG;
+  if (((uintptr_t)d_hist & 3u) || ((uintptr_t)d_rects & 3u) || ((uintptr_t)d_hist_out & 3u))
+    return IHIST_ERR_INVALID_ARG;
+  if ((unsigned long long)n * (unsigned long long)B > 0x7fffffffull) return IHIST_ERR_UNSUPPORTED;
+  const unsigned int total = (unsigned int)n * (unsigned int)B;
+  const unsigned int threads = 256;
+  const unsigned int grid =
+      std::min<unsigned int>((total + threads - 1) / threads, (unsigned int)sms * 16u);
+  if (layout == IHIST_BIN_MAJOR)
+    query_kernel<0><<<grid, threads, 0, (cudaStream_t)stream>>>(d_hist, H, W, B, d_rects, total,
+                                                                d_hist_out, ctrl);
+  else
+    query_kernel<1><<<grid, threads, 0, (cudaStream_t)stream>>>(d_hist, H, W, B, d_rects, total,
+                                                                d_hist_out, ctrl);
   if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
   return IHIST_OK;
 }
@@ -301,24 +417,10 @@ extern "C" int ihist_query(ihist_plan_t p, const uint32_t *d_hist, const int32_t
                            uint32_t *d_hist_out, void *stream) {
   if (!p || n < 0) return IHIST_ERR_INVALID_ARG;
   if (n == 0) return IHIST_OK;
-  if (!d_hist || !d_rects || !d_hist_out) return IHIST_ERR_INVALID_ARG;
-  if (((uintptr_t)d_hist & 3u) || ((uintptr_t)d_rects & 3u) || ((uintptr_t)d_hist_out & 3u))
-    return IHIST_ERR_INVALID_ARG;
-  if ((unsigned long long)n * (unsigned long long)p->B > 0x7fffffffull) return IHIST_ERR_UNSUPPORTED;
   int rc = check_device(p);
   if (rc != IHIST_OK) return rc;
-  const unsigned int total = (unsigned int)n * (unsigned int)p->B;
-  const unsigned int threads = 256;
-  const unsigned int grid =
-      std::min<unsigned int>((total + threads - 1) / threads, (unsigned int)p->sms * 16u);
-  if (p->layout == IHIST_BIN_MAJOR)
-    query_kernel<0><<<grid, threads, 0, (cudaStream_t)stream>>>(d_hist, p->H, p->W, p->B, d_rects,
-                                                                total, d_hist_out, p->ctrl);
-  else
-    query_kernel<1><<<grid, threads, 0, (cudaStream_t)stream>>>(d_hist, p->H, p->W, p->B, d_rects,
-                                                                total, d_hist_out, p->ctrl);
-  if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
-  return IHIST_OK;
+  return launch_query(p->H, p->W, p->B, p->layout, p->sms, p->ctrl, d_hist, d_rects, n, d_hist_out,
+                      stream);
 }
 
 extern "C" int ihist_sequence_host(ihist_plan_t p, const uint8_t *h_frames, size_t frame_stride,
@@ -363,19 +465,23 @@ extern "C" int ihist_sequence_host(ihist_plan_t p, const uint8_t *h_frames, size
   return IHIST_OK;
 }
 
+static int read_status(Ctrl *ctrl, void *stream, int *device_status) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int v = 0;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return IHIST_ERR_CUDA;
+  if (cudaMemcpy(&v, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return IHIST_ERR_CUDA;
+  if (cudaMemset(&ctrl->status, 0, sizeof(int)) != cudaSuccess) return IHIST_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return IHIST_ERR_CUDA;
+  *device_status = v;
+  return IHIST_OK;
+}
+
 extern "C" int ihist_status(ihist_plan_t p, void *stream, int *device_status) {
   if (!p || !device_status) return IHIST_ERR_INVALID_ARG;
   int rc = check_device(p);
   if (rc != IHIST_OK) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
-  int v = 0;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return IHIST_ERR_CUDA;
-  if (cudaMemcpy(&v, &p->ctrl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return IHIST_ERR_CUDA;
-  if (cudaMemset(&p->ctrl->status, 0, sizeof(int)) != cudaSuccess) return IHIST_ERR_CUDA;
-  if (cudaDeviceSynchronize() != cudaSuccess) return IHIST_ERR_CUDA;
-  *device_status = v;
-  return IHIST_OK;
+  return read_status(p->ctrl, stream, device_status);
 }
 
 extern "C" void ihist_destroy(ihist_plan_t p) {
@@ -391,3 +497,419 @@ extern "C" void ihist_destroy(ihist_plan_t p) {
   if (prev != p->device && prev >= 0) cudaSetDevice(prev);
   delete p;
 }
+
+// ---------------------------------------------------------------- batches
+
+namespace {
+
+constexpr int kBatchWarps = 16;     // warps per CTA of the batched kernel
+constexpr int kBatchDefaultRows = 32;
+
+// Per-frame tiling inside a 16-warp CTA: the chunks-per-warp m (1, 2 or 4)
+// and bin groups per CTA that keep the most warps busy, smaller m on ties.
+void batch_frame_tiling(int h, int w, int nbins, int G, int R_req, FrameDesc *f) {
+  const int nchunks = (w + kChunk - 1) / kChunk;
+  const int ngroups = (nbins + G - 1) / G;
+  double best = -1.0;
+  int bm = 1, bwpg = nchunks, bgpc = 1;
+  for (int m = 1; m <= 4; m <<= 1) {
+    const int wpg = (nchunks + m - 1) / m;
+    if (wpg > kBatchWarps) continue;
+    const int gpc = std::max(1, std::min(ngroups, kBatchWarps / wpg));
+    const double util = (double)nchunks * gpc / ((double)kBatchWarps * m);
+    if (util > best + 1e-9) {
+      best = util;
+      bm = m;
+      bwpg = wpg;
+      bgpc = gpc;
+    }
+  }
+  f->H = h;
+  f->W = w;
+  f->B = nbins;
+  f->R = std::min(R_req > 0 ? R_req : kBatchDefaultRows, h);
+  f->nbands = (h + f->R - 1) / f->R;
+  f->ngroups = ngroups;
+  f->nchunks = nchunks;
+  f->m = bm;
+  f->wpg = bwpg;
+  f->gpc = bgpc;
+  f->ngsets = (ngroups + bgpc - 1) / bgpc;
+  f->nitems = (unsigned int)f->nbands * (unsigned int)f->ngsets;
+  f->fault_skip_band = -1;
+}
+
+bool frame_tma_ok(const ihist_frame_t &fr) {
+  return !((uintptr_t)fr.d_in & 15u) && !(fr.in_pitch & 15u) && fr.w >= kChunk &&
+         fr.in_pitch < (1ull << 40);
+}
+
+bool frame_vec_ok(const ihist_frame_t &fr) {
+  return fr.w % 4 == 0 && !((uintptr_t)fr.d_out & 15u);
+}
+
+}  // namespace
+
+struct ihist_batch_s {
+  int device, sms, n, G, mmax, R_max, ncg_max, ctas_per_sm;
+  bool tma, vec;
+  unsigned int timeout_us, total;
+  size_t smem_bytes, ws_bytes;
+  void *ws;
+  Ctrl *ctrl;
+  FrameDesc *d_fd;
+  CUtensorMap *d_tm;
+  unsigned int *d_end;
+  std::vector<FrameDesc> fd;
+  std::vector<ihist_frame_t> io;
+  FrameDesc *h_fd;     // pinned staging for set_io
+  CUtensorMap *h_tm;   // pinned staging for set_io
+  cudaEvent_t staged;  // last staging copy done
+  cudaEvent_t uploaded, computed;  // upload/compute pipeline
+  unsigned int *d_bins_end;        // prefix sums of bin counts (queries)
+  unsigned long long bins_total;
+  bool launched;                   // a compute has been enqueued
+};
+
+static bool encode_frame_map(const ihist_frame_t &fr, int R, CUtensorMap *map) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t gdim[2] = {(cuuint64_t)fr.w, (cuuint64_t)fr.h};
+  cuuint64_t gstride[1] = {(cuuint64_t)fr.in_pitch};
+  cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)R};
+  cuuint32_t estride[2] = {1u, 1u};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(fr.d_in), gdim, gstride,
+             box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Fill the host copies of descriptors and tensor maps for the given I/O.
+static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames) {
+  for (int i = 0; i < b->n; ++i) {
+    const ihist_frame_t &fr = frames[i];
+    FrameDesc &f = b->fd[i];
+    if (fr.h != f.H || fr.w != f.W || fr.nbins != f.B || fr.layout != f.layout)
+      return IHIST_ERR_INVALID_ARG;
+    if (!fr.d_in || !fr.d_out || fr.in_pitch < (size_t)fr.w || ((uintptr_t)fr.d_out & 3u))
+      return IHIST_ERR_INVALID_ARG;
+    if (b->tma && !frame_tma_ok(fr)) return IHIST_ERR_INVALID_ARG;
+    if (b->vec && !frame_vec_ok(fr)) return IHIST_ERR_INVALID_ARG;
+    f.in = fr.d_in;
+    f.pitch = (long long)fr.in_pitch;
+    f.out = fr.d_out;
+    b->io[i] = fr;
+    b->h_fd[i] = f;
+    if (b->tma) {
+      if (!encode_frame_map(fr, f.R, &b->h_tm[i])) return IHIST_ERR_CUDA;
+    } else {
+      std::memset(&b->h_tm[i], 0, sizeof(CUtensorMap));
+    }
+  }
+  return IHIST_OK;
+}
+
+extern "C" void ihist_batch_destroy(ihist_batch_t b) {
+  if (!b) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != b->device) cudaSetDevice(b->device);
+  if (b->staged) cudaEventDestroy(b->staged);
+  if (b->uploaded) cudaEventDestroy(b->uploaded);
+  if (b->computed) cudaEventDestroy(b->computed);
+  if (b->h_fd) cudaFreeHost(b->h_fd);
+  if (b->h_tm) cudaFreeHost(b->h_tm);
+  if (b->ws) cudaFree(b->ws);
+  if (prev != b->device && prev >= 0) cudaSetDevice(prev);
+  delete b;
+}
+
+extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_tune_t *tune,
+                                ihist_batch_t *out) {
+  if (!frames || n < 1 || !out) return IHIST_ERR_INVALID_ARG;
+  ihist_tune_t t;
+  std::memset(&t, 0, sizeof(t));
+  if (tune) t = *tune;
+  if (t.bins_per_cta == 0) t.bins_per_cta = 4;
+  if (t.bins_per_cta != 4 && t.bins_per_cta != 8) return IHIST_ERR_INVALID_ARG;
+  if (t.rows_per_band < 0 || t.rows_per_band > 255) return IHIST_ERR_INVALID_ARG;
+  if (t.ctas_per_sm < 0 || t.ctas_per_sm > 32) return IHIST_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const int rc = validate_shape(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout);
+    if (rc != IHIST_OK) return rc;
+  }
+  int dev = 0, sms = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IHIST_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return IHIST_ERR_CUDA;
+
+  ihist_batch_s *b = new (std::nothrow) ihist_batch_s();
+  if (!b) return IHIST_ERR_OOM;
+  b->device = dev;
+  b->sms = sms;
+  b->n = n;
+  b->G = t.bins_per_cta;
+  b->timeout_us = t.timeout_us ? t.timeout_us : kDefaultTimeoutUs;
+  b->fd.resize(n);
+  b->io.resize(n);
+  b->tma = true;
+  b->vec = true;
+  int mmax = 1;
+  std::vector<unsigned int> ends(n);
+  unsigned long long total = 0;
+  size_t nci_total = 0;
+  // default rows per band: the largest R (at most 64) whose shared memory
+  // (16 warps x R rows of staged input and row carries) fits two CTAs per SM
+  int R_req = t.rows_per_band;
+  if (R_req == 0) {
+    int smem_sm = 0;
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+      delete b;
+      return IHIST_ERR_CUDA;
+    }
+    int ncg = 1;
+    for (int i = 0; i < n; ++i) ncg = std::max(ncg, (frames[i].w + kChunk - 1) / kChunk * 16);
+    R_req = 8;
+    for (int r = 64; r >= 8; --r)
+      if (2 * (smem_layout(kBatchWarps, r, b->G, ncg).bytes + 1024) <= (size_t)smem_sm) {
+        R_req = r;
+        break;
+      }
+  }
+  for (int i = 0; i < n; ++i) {
+    FrameDesc &f = b->fd[i];
+    std::memset(&f, 0, sizeof(f));
+    batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, b->G, R_req, &f);
+    f.layout = frames[i].layout;
+    mmax = std::max(mmax, f.m);
+    b->R_max = std::max(b->R_max, f.R);
+    b->ncg_max = std::max(b->ncg_max, f.nchunks * f.gpc);
+    total += f.nitems;
+    ends[i] = (unsigned int)total;
+    nci_total += (size_t)f.nbands * f.ngroups * f.nchunks;
+    b->tma = b->tma && frame_tma_ok(frames[i]);
+    b->vec = b->vec && frame_vec_ok(frames[i]);
+  }
+  if (total >= 0xffffffffull) {
+    delete b;
+    return IHIST_ERR_UNSUPPORTED;
+  }
+  b->total = (unsigned int)total;
+  b->mmax = mmax_for(mmax);
+  BatchFn fn = batch_fn(b->G, b->mmax, b->tma, b->vec);
+  if (!fn) {
+    delete b;
+    return IHIST_ERR_UNSUPPORTED;
+  }
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return IHIST_ERR_CUDA;
+  }
+  const size_t dyn_max = (size_t)optin > a.sharedSizeBytes ? (size_t)optin - a.sharedSizeBytes : 0;
+  b->smem_bytes = smem_layout(kBatchWarps, b->R_max, b->G, b->ncg_max).bytes;
+  if (b->smem_bytes > dyn_max ||
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return IHIST_ERR_UNSUPPORTED;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBatchWarps * 32, b->smem_bytes) !=
+          cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    delete b;
+    return IHIST_ERR_UNSUPPORTED;
+  }
+  b->ctas_per_sm = t.ctas_per_sm > 0 ? std::min(t.ctas_per_sm, occ) : occ;
+
+  // workspace: control, descriptors, tensor maps, item ends, then per-frame carries
+  size_t off = 0;
+  const size_t o_ctrl = off;
+  off = align_up(off + sizeof(Ctrl), 256);
+  const size_t o_fd = off;
+  off = align_up(off + (size_t)n * sizeof(FrameDesc), 256);
+  const size_t o_tm = off;
+  off = align_up(off + (size_t)n * sizeof(CUtensorMap), 256);
+  const size_t o_end = off;
+  off = align_up(off + (size_t)n * sizeof(unsigned int), 256);
+  const size_t o_bend = off;
+  off = align_up(off + (size_t)n * sizeof(unsigned int), 256);
+  const size_t o_flags = off;
+  off = align_up(off + nci_total * sizeof(uint32_t), 256);
+  const size_t zero_bytes = off;
+  const size_t o_carry = off;
+  for (int i = 0; i < n; ++i) {
+    const FrameDesc &f = b->fd[i];
+    const size_t nci = (size_t)f.nbands * f.ngroups * f.nchunks;
+    off = align_up(off + nci * kChunk * (b->G / 4) * 4, 256);
+    off = align_up(off + nci * b->G * 4, 256);
+    off = align_up(off + nci * b->G * kChunk * 4, 256);
+  }
+  b->ws_bytes = off;
+  if (cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess ||
+      cudaMallocHost((void **)&b->h_fd, (size_t)n * sizeof(FrameDesc)) != cudaSuccess ||
+      cudaMallocHost((void **)&b->h_tm, (size_t)n * sizeof(CUtensorMap)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->computed, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    ihist_batch_destroy(b);
+    return IHIST_ERR_OOM;
+  }
+  char *base = static_cast<char *>(b->ws);
+  b->ctrl = reinterpret_cast<Ctrl *>(base + o_ctrl);
+  b->d_fd = reinterpret_cast<FrameDesc *>(base + o_fd);
+  b->d_tm = reinterpret_cast<CUtensorMap *>(base + o_tm);
+  b->d_end = reinterpret_cast<unsigned int *>(base + o_end);
+  b->d_bins_end = reinterpret_cast<unsigned int *>(base + o_bend);
+  std::vector<unsigned int> bins_end(n);
+  unsigned long long bsum = 0;
+  for (int i = 0; i < n; ++i) {
+    bsum += (unsigned long long)frames[i].nbins;
+    bins_end[i] = (unsigned int)bsum;
+  }
+  b->bins_total = bsum;
+  size_t fo = o_flags, co = o_carry;
+  for (int i = 0; i < n; ++i) {
+    FrameDesc &f = b->fd[i];
+    const size_t nci = (size_t)f.nbands * f.ngroups * f.nchunks;
+    f.flags = reinterpret_cast<uint32_t *>(base + fo);
+    fo += nci * sizeof(uint32_t);
+    f.agg_cnt = reinterpret_cast<uint32_t *>(base + co);
+    co = align_up(co + nci * kChunk * (b->G / 4) * 4, 256);
+    f.agg_left = reinterpret_cast<uint32_t *>(base + co);
+    co = align_up(co + nci * b->G * 4, 256);
+    f.incl = reinterpret_cast<uint32_t *>(base + co);
+    co = align_up(co + nci * b->G * kChunk * 4, 256);
+  }
+  int rc = batch_bind(b, frames);
+  if (rc != IHIST_OK) {
+    ihist_batch_destroy(b);
+    return rc;
+  }
+  // clear the control block and the flags only; the descriptor arrays
+  // between them are written once by the copies below
+  if (cudaMemset(b->ws, 0, sizeof(Ctrl)) != cudaSuccess ||
+      cudaMemset(base + o_flags, 0, zero_bytes - o_flags) != cudaSuccess ||
+      cudaMemcpy(b->d_fd, b->h_fd, (size_t)n * sizeof(FrameDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_tm, b->h_tm, (size_t)n * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_end, ends.data(), (size_t)n * sizeof(unsigned int), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(b->d_bins_end, bins_end.data(), (size_t)n * sizeof(unsigned int),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    ihist_batch_destroy(b);
+    return IHIST_ERR_CUDA;
+  }
+  *out = b;
+  return IHIST_OK;
+}
+
+static int check_batch_device(const ihist_batch_s *b) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IHIST_ERR_CUDA;
+  return dev == b->device ? IHIST_OK : IHIST_ERR_INVALID_ARG;
+}
+
+extern "C" int ihist_batch_set_io(ihist_batch_t b, const ihist_frame_t *frames, int n, void *stream) {
+  if (!b || !frames || n != b->n) return IHIST_ERR_INVALID_ARG;
+  int rc = check_batch_device(b);
+  if (rc != IHIST_OK) return rc;
+  // the staging buffers may still feed the previous copy
+  if (cudaEventSynchronize(b->staged) != cudaSuccess) return IHIST_ERR_CUDA;
+  std::vector<ihist_frame_t> keep(b->io);
+  rc = batch_bind(b, frames);
+  if (rc != IHIST_OK) {
+    batch_bind(b, keep.data());
+    return rc;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(b->d_fd, b->h_fd, (size_t)n * sizeof(FrameDesc), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(b->d_tm, b->h_tm, (size_t)n * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaEventRecord(b->staged, s) != cudaSuccess)
+    return IHIST_ERR_CUDA;
+  return IHIST_OK;
+}
+
+extern "C" int ihist_batch_compute(ihist_batch_t b, void *stream) {
+  if (!b) return IHIST_ERR_INVALID_ARG;
+  int rc = check_batch_device(b);
+  if (rc != IHIST_OK) return rc;
+  BatchFn fn = batch_fn(b->G, b->mmax, b->tma, b->vec);
+  const unsigned int grid = std::min<unsigned int>(b->total, (unsigned int)(b->ctas_per_sm * b->sms));
+  const unsigned long long timeout_ns = (unsigned long long)b->timeout_us * 1000ull;
+  fn<<<grid, kBatchWarps * 32, b->smem_bytes, (cudaStream_t)stream>>>(
+      b->d_fd, b->d_tm, b->d_end, b->n, b->R_max, b->ncg_max, b->ctrl, timeout_ns);
+  if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
+  if (cudaEventRecord(b->computed, (cudaStream_t)stream) != cudaSuccess) return IHIST_ERR_CUDA;
+  b->launched = true;
+  return IHIST_OK;
+}
+
+extern "C" int ihist_batch_upload_compute(ihist_batch_t b, const uint8_t *const *h_frames, void *stream,
+                                          void *copy_stream) {
+  if (!b || !h_frames) return IHIST_ERR_INVALID_ARG;
+  for (int i = 0; i < b->n; ++i)
+    if (!h_frames[i]) return IHIST_ERR_INVALID_ARG;
+  int rc = check_batch_device(b);
+  if (rc != IHIST_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream, cs = (cudaStream_t)copy_stream;
+  // inputs are overwritten only after the previous compute of this batch read them
+  if (b->launched && cudaStreamWaitEvent(cs, b->computed, 0) != cudaSuccess) return IHIST_ERR_CUDA;
+  for (int i = 0; i < b->n; ++i) {
+    const ihist_frame_t &fr = b->io[i];
+    if (cudaMemcpy2DAsync(const_cast<uint8_t *>(fr.d_in), fr.in_pitch, h_frames[i], (size_t)fr.w,
+                          (size_t)fr.w, (size_t)fr.h, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+      return IHIST_ERR_CUDA;
+  }
+  if (cudaEventRecord(b->uploaded, cs) != cudaSuccess ||
+      cudaStreamWaitEvent(s, b->uploaded, 0) != cudaSuccess)
+    return IHIST_ERR_CUDA;
+  return ihist_batch_compute(b, stream);
+}
+
+extern "C" int ihist_batch_query_all(ihist_batch_t b, const int32_t *d_rects, int n, uint32_t *d_out,
+                                     void *stream) {
+  if (!b || n < 0) return IHIST_ERR_INVALID_ARG;
+  if (n == 0) return IHIST_OK;
+  if (!d_rects || !d_out || ((uintptr_t)d_rects & 3u) || ((uintptr_t)d_out & 3u))
+    return IHIST_ERR_INVALID_ARG;
+  int rc = check_batch_device(b);
+  if (rc != IHIST_OK) return rc;
+  if (b->bins_total * (unsigned long long)n >= (1ull << 40)) return IHIST_ERR_UNSUPPORTED;
+  const unsigned long long total = b->bins_total * (unsigned long long)n;
+  const unsigned int threads = 256;
+  const unsigned long long want = (total + threads - 1) / threads;
+  const unsigned int grid = (unsigned int)std::min<unsigned long long>(want, (unsigned long long)b->sms * 16ull);
+  query_batch_kernel<FrameDesc><<<grid, threads, 0, (cudaStream_t)stream>>>(
+      b->d_fd, b->d_bins_end, b->n, d_rects, (unsigned int)n, total, d_out, b->ctrl);
+  if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
+  return IHIST_OK;
+}
+
+extern "C" int ihist_batch_query(ihist_batch_t b, int frame, const uint32_t *d_hist,
+                                 const int32_t *d_rects, int n, uint32_t *d_hist_out, void *stream) {
+  if (!b || frame < 0 || frame >= b->n || n < 0) return IHIST_ERR_INVALID_ARG;
+  if (n == 0) return IHIST_OK;
+  int rc = check_batch_device(b);
+  if (rc != IHIST_OK) return rc;
+  const FrameDesc &f = b->fd[frame];
+  return launch_query(f.H, f.W, f.B, f.layout, b->sms, b->ctrl, d_hist, d_rects, n, d_hist_out, stream);
+}
+
+extern "C" int ihist_batch_status(ihist_batch_t b, void *stream, int *device_status) {
+  if (!b || !device_status) return IHIST_ERR_INVALID_ARG;
+  int rc = check_batch_device(b);
+  if (rc != IHIST_OK) return rc;
+  return read_status(b->ctrl, stream, device_status);
+}
+
+extern "C" size_t ihist_batch_workspace_bytes(ihist_batch_t b) { return b ? b->ws_bytes : 0; }
+
+extern "C" unsigned int ihist_batch_items(ihist_batch_t b) { return b ? b->total : 0u; }

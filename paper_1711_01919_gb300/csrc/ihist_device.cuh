@@ -49,6 +49,20 @@ __device__ __forceinline__ uint4 ld_relaxed_v4(const uint32_t *p) {
   return v;
 }
 
+// Coherent 32-bit / 64-bit loads (L2, never a possibly stale L1 or
+// read-only-cache line) for descriptors that other agents wrote.
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const void *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const void *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Streaming (evict-first) 128-bit store for the write-once output.
 __device__ __forceinline__ void st_stream_v4(uint32_t *p, uint32_t a, uint32_t b, uint32_t c,
                                              uint32_t d) {
@@ -119,6 +133,69 @@ __device__ __forceinline__ uint32_t wait_flag(const uint32_t *flag, uint32_t epo
     }
     __nanosleep(backoff);
     if (backoff < 1024) backoff <<= 1;
+  }
+}
+
+// ---- TMA + mbarrier (per-warp tile staging) ------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Make mbarrier initialisation visible to the async (TMA) proxy.
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Order this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) writes to the same buffer.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One lane: arm the barrier for `bytes` and start a 2-D tiled TMA load of
+// the box at (x, y) (x in elements, x * 1 byte a multiple of 16) into dst.
+__device__ __forceinline__ void tma_load_2d(const void *tmap, void *dst, uint64_t *bar, int x, int y,
+                                            uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Wait for the barrier phase with the given parity.  Bounded: gives up
+// after timeout_ns (returns false), so a lost completion cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long timeout_ns) {
+  const uint32_t a = smem_u32(bar);
+  unsigned long long t0 = 0;
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    const unsigned long long now = global_ns();
+    if (t0 == 0) {
+      t0 = now;
+    } else if (now - t0 > timeout_ns) {
+      return false;
+    }
   }
 }
 

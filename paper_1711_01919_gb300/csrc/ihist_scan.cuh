@@ -20,33 +20,63 @@
 //   * a5 store: each output word is written once, 128-bit streaming stores.
 //
 // Work item = (band k of R rows, bin group g of G bins).  The CTA's warps
-// split the frame width: warp w owns 128-column chunks [w*m, w*m + m).  The
-// horizontal carry between warps comes from a counting pass (per-row bin
-// totals of each warp's columns, reduced with one redux.sync per 4 bins)
-// and an exclusive scan over warps in shared memory.  The vertical carry
-// between bands is the look-back, per (band, group, chunk).
+// split the frame width: warp w owns 128-column chunks [w*m, w*m + m).  Each
+// warp stages its chunk's R x 128-byte input tile in shared memory (a TMA
+// tensor copy when the frame is 16-byte aligned, else plain loads) and reads
+// it once to count and once to emit.  The horizontal carry between warps
+// comes from the counting pass (per-row bin totals of each warp's columns,
+// one redux.sync per 4 bins) and an exclusive scan over warps in shared
+// memory.  The vertical carry between bands is the look-back, per (band,
+// group, chunk).
 #pragma once
+
+#include <cuda.h>
 
 #include "ihist_device.cuh"
 
 namespace ihist {
 
 // One frame as the kernel sees it.  Offsets of the carry buffers are in
-// units of "chunk items": ci = (item * nchunks + chunk), item = k*ngroups + g.
+// units of "chunk items": ci = ((k * ngroups + g) * nchunks + chunk) for band
+// k, bin group g.  A work item is (band k, set of gpc bin groups).
 struct FrameDesc {
   const uint8_t *in;
   long long pitch;      // bytes between rows of in
   uint32_t *out;
   int H, W, B, layout;  // layout: 0 bin-major, 1 pixel-major
   int R, nbands, ngroups, nchunks, m;
+  int wpg;              // warps per bin group: ceil(nchunks / m)
+  int gpc;              // bin groups per CTA (warp w serves group w / wpg)
+  int ngsets;           // ceil(ngroups / gpc)
   int fault_skip_band;  // -1 off
-  unsigned int nitems;  // nbands * ngroups
-  unsigned int pad0;
+  unsigned int nitems;  // nbands * ngsets
   uint32_t *agg_cnt;    // [ci][128 cols][G/4] words: packed column counts (bytes)
   uint32_t *agg_left;   // [ci][G]: band count left of the chunk
   uint32_t *incl;       // [ci][G][128]: H on the band's last row
   uint32_t *flags;      // [ci]
 };
+
+// Dynamic shared memory of one CTA, carved from a 128-byte aligned base.
+struct SmemLayout {
+  uint32_t tile_off, row_off, ctot_off, bar_off, bytes;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int NW, int R, int G, int nchunks) {
+  SmemLayout L;
+  uint32_t off = 0;
+  L.tile_off = off;  // [NW][R][128] bytes
+  off += (uint32_t)NW * (uint32_t)R * kChunk;
+  off = (off + 15u) & ~15u;
+  L.row_off = off;  // [NW][R][G] u32
+  off += (uint32_t)NW * (uint32_t)R * (uint32_t)G * 4u;
+  L.ctot_off = off;  // [groups per CTA][nchunks][G] u32 (nchunks passed as gpc * nchunks)
+  off += (uint32_t)nchunks * (uint32_t)G * 4u;
+  off = (off + 7u) & ~7u;
+  L.bar_off = off;  // [NW] mbarriers
+  off += (uint32_t)NW * 8u;
+  L.bytes = off + 128u;  // + base alignment slack
+  return L;
+}
 
 // Bit offset 8*q of the pixel's bin relative to the CTA's first bin
 // (gbase = 8 * g * G); an invalid column gets an offset that no sub-group
@@ -57,29 +87,7 @@ __device__ __forceinline__ uint32_t bin_offset(uint32_t v, uint32_t nbins, uint3
 
 constexpr uint32_t kNoBin = 0x80000000u;
 
-// Four consecutive pixels of one row starting at column x (x % 4 == 0).
-template <bool VEC>
-__device__ __forceinline__ void load_offsets(const uint8_t *__restrict__ row, int x, int W,
-                                             uint32_t nbins, uint32_t gbase, uint32_t u[4]) {
-  if (VEC) {
-    // VEC: row start 4-byte aligned and W % 4 == 0, so a lane is all-in or all-out.
-    if (x < W) {
-      const uint32_t px = __ldg(reinterpret_cast<const unsigned int *>(row + x));
-#pragma unroll
-      for (int i = 0; i < 4; ++i) u[i] = bin_offset(__byte_perm(px, 0u, 0x4440u + i), nbins, gbase);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) u[i] = kNoBin;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      u[i] = (x + i < W) ? bin_offset(__ldg(row + x + i), nbins, gbase) : kNoBin;
-  }
-}
-
-// Exclusive/inclusive scan helpers on 4 columns x one 32-bit value per lane.
-// Returns the inclusive prefix of v[0..3] over the 128-column chunk.
+// Inclusive prefix of v[0..3] (this lane's 4 columns) over the 128-column chunk.
 __device__ __forceinline__ void chunk_scan32(uint32_t v[4], int lane) {
   v[1] += v[0];
   v[2] += v[1];
@@ -92,28 +100,86 @@ __device__ __forceinline__ void chunk_scan32(uint32_t v[4], int lane) {
   v[3] = t;
 }
 
+// Bin offsets of this lane's 4 pixels in tile row yl (columns x .. x+3).
+__device__ __forceinline__ void tile_offsets(const uint8_t *tile, int yl, int lane, int x, int W,
+                                             uint32_t nbins, uint32_t gbase, uint32_t u[4]) {
+  const uint32_t px = *reinterpret_cast<const uint32_t *>(tile + yl * kChunk + 4 * lane);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    u[i] = (x + i < W) ? bin_offset(__byte_perm(px, 0u, 0x4440u + i), nbins, gbase) : kNoBin;
+}
+
+// Stage rows y0 .. y0+nrows-1, columns c*128 .. c*128+127 of the frame into
+// this warp's tile.  TMA: one lane issues a tensor copy and the warp waits
+// on the tile's mbarrier (bounded).  Otherwise: each lane copies its 4 bytes
+// of every row with plain loads.  Columns past W are don't-care (masked by
+// the x < W tests).  Returns false if the wait timed out.
+template <bool TMA>
+__device__ __forceinline__ bool stage_tile(const FrameDesc &f, const CUtensorMap *tmap, uint8_t *tile,
+                                           uint64_t *bar, uint32_t &phase, int y0, int nrows, int c,
+                                           int lane, unsigned long long timeout_ns) {
+  if (TMA) {
+    __syncwarp();  // every lane is done reading the previous tile
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      tma_load_2d(tmap, tile, bar, c * kChunk, y0, (uint32_t)f.R * kChunk);
+    }
+    const bool ok = mbar_wait(bar, phase, timeout_ns);
+    phase ^= 1u;
+    return __all_sync(kFull, ok);
+  } else {
+    __syncwarp();
+    const int x = c * kChunk + 4 * lane;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(f.in) | (uintptr_t)f.pitch) & 3u) == 0;
+#pragma unroll 4
+    for (int yl = 0; yl < nrows; ++yl) {
+      const uint8_t *src = f.in + (long long)(y0 + yl) * f.pitch + x;
+      uint32_t v = 0u;
+      if (aligned && x + 3 < f.W) {
+        v = __ldg(reinterpret_cast<const unsigned int *>(src));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (x + i < f.W) v |= (uint32_t)__ldg(src + i) << (8 * i);
+      }
+      *reinterpret_cast<uint32_t *>(tile + yl * kChunk + 4 * lane) = v;
+    }
+    __syncwarp();
+    return true;
+  }
+}
+
 // ---------------------------------------------------------------------------
-// One work item: band k, bin group g.  smem layout (32-bit words):
-//   s_row [NW][R][G]   per-warp per-row bin totals, then row carries
-//   s_ctot[nchunks][G] per-chunk band totals, then their exclusive prefix
-template <int G, int MMAX, bool VEC>
-__device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it, uint32_t epoch,
-                                             Ctrl *ctrl, unsigned long long timeout_ns,
-                                             uint32_t *s_row, uint32_t *s_ctot) {
+// One work item: band k, bin group g.
+template <int G, int MMAX, bool TMA, bool VEC>
+__device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorMap *tmap,
+                                             unsigned int it, uint32_t epoch, Ctrl *ctrl,
+                                             unsigned long long timeout_ns, uint8_t *s_tiles,
+                                             uint32_t *s_row, uint32_t *s_ctot, uint64_t *s_bar,
+                                             uint32_t &phase) {
   constexpr int GQ = G / 4;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  const int NW = blockDim.x >> 5;
-  const int k = (int)(it / (unsigned)f.ngroups);
-  const int g = (int)(it % (unsigned)f.ngroups);
+  const int k = (int)(it / (unsigned)f.ngsets);
+  const int gs = (int)(it % (unsigned)f.ngsets);
+  const int lg = w / f.wpg;  // local bin group of this warp
+  const int wg = w % f.wpg;  // warp slot within the group
+  const int g = gs * f.gpc + lg;
+  const bool gvalid = (lg < f.gpc) && (g < f.ngroups);
   const int y0 = k * f.R;
   const int nrows = min(f.R, f.H - y0);
   const uint32_t nbins = (uint32_t)f.B;
   const uint32_t gbase = 8u * (uint32_t)(g * G);
-  const int c_begin = w * f.m;
-  const int my_m = max(0, min(f.m, f.nchunks - c_begin));  // warp-uniform
+  const int c_begin = wg * f.m;
+  const int my_m = gvalid ? max(0, min(f.m, f.nchunks - c_begin)) : 0;  // warp-uniform
   const bool publish = (k != f.fault_skip_band);
-  const unsigned int ci0 = it * (unsigned)f.nchunks;        // chunk-item of chunk 0
+  const unsigned int ci0 = ((unsigned)k * f.ngroups + g) * (unsigned)f.nchunks;  // chunk 0
+  uint32_t *my_ctot = s_ctot + (size_t)(gvalid ? lg : 0) * f.nchunks * G;
+  uint8_t *tile = s_tiles + (size_t)w * f.R * kChunk;
+  uint64_t *bar = s_bar + w;
+  uint32_t *myrow = s_row + (size_t)w * f.R * G;
+  bool stage_ok = true;
+  int staged = -1;  // chunk currently held in this warp's tile
 
   // ---- counting pass: column counts (bytes) and per-row segment totals ----
   uint32_t colcnt[MMAX][GQ][4];
@@ -124,45 +190,45 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
 #pragma unroll
       for (int i = 0; i < 4; ++i) colcnt[cc][q][i] = 0u;
 
-  for (int yl = 0; yl < nrows; ++yl) {
-    const uint8_t *row = f.in + (long long)(y0 + yl) * f.pitch;
-    uint32_t rs[GQ];
+  if (my_m == 0) {
+    for (int e = lane; e < nrows * G; e += 32) myrow[e] = 0u;
+  }
 #pragma unroll
-    for (int q = 0; q < GQ; ++q) rs[q] = 0u;
-#pragma unroll
-    for (int cc = 0; cc < MMAX; ++cc) {
-      if (cc < my_m) {
+  for (int cc = 0; cc < MMAX; ++cc) {
+    if (cc < my_m) {
+      const int c = c_begin + cc;
+      const int x = c * kChunk + 4 * lane;
+      stage_ok &= stage_tile<TMA>(f, tmap, tile, bar, phase, y0, nrows, c, lane, timeout_ns);
+      staged = c;
+#pragma unroll 4
+      for (int yl = 0; yl < nrows; ++yl) {
         uint32_t u[4];
-        load_offsets<VEC>(row, (c_begin + cc) * kChunk + 4 * lane, f.W, nbins, gbase, u);
+        tile_offsets(tile, yl, lane, x, f.W, nbins, gbase, u);
 #pragma unroll
-        for (int q = 0; q < GQ; ++q)
+        for (int q = 0; q < GQ; ++q) {
+          uint32_t rs = 0u;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const uint32_t ind = shl_clamp(1u, u[i] - 32u * q);
             colcnt[cc][q][i] += ind;
-            rs[q] += ind;
+            rs += ind;
           }
-      }
-    }
-    uint32_t *dst = s_row + ((size_t)w * f.R + yl) * G;
-    if (my_m > 0) {
-#pragma unroll
-      for (int q = 0; q < GQ; ++q) {
-        uint32_t t0, t1, t2, t3;
-        if (MMAX == 1) {
-          // one chunk: each byte sums at most 4 x 32 = 128
-          const uint32_t t = __reduce_add_sync(kFull, rs[q]);
-          t0 = t & 0xffu; t1 = (t >> 8) & 0xffu; t2 = (t >> 16) & 0xffu; t3 = t >> 24;
-        } else {
-          const uint32_t lo = __reduce_add_sync(kFull, __byte_perm(rs[q], 0u, 0x4140u));
-          const uint32_t hi = __reduce_add_sync(kFull, __byte_perm(rs[q], 0u, 0x4342u));
-          t0 = lo & 0xffffu; t1 = lo >> 16; t2 = hi & 0xffffu; t3 = hi >> 16;
+          // row total of this chunk, four bins in bytes (each at most 128)
+          const uint32_t t = __reduce_add_sync(kFull, rs);
+          if (lane == 0) {
+            uint4 *d = reinterpret_cast<uint4 *>(myrow + (size_t)yl * G + 4 * q);
+            uint4 v = make_uint4(t & 0xffu, (t >> 8) & 0xffu, (t >> 16) & 0xffu, t >> 24);
+            if (cc > 0) {
+              const uint4 o = *d;
+              v.x += o.x;
+              v.y += o.y;
+              v.z += o.z;
+              v.w += o.w;
+            }
+            *d = v;
+          }
         }
-        if (lane == 0) *reinterpret_cast<uint4 *>(dst + 4 * q) = make_uint4(t0, t1, t2, t3);
       }
-    } else if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < GQ; ++q) *reinterpret_cast<uint4 *>(dst + 4 * q) = make_uint4(0, 0, 0, 0);
     }
   }
 
@@ -182,7 +248,7 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
         lo = __reduce_add_sync(kFull, lo);  // at most 128R <= 32640 per lane
         hi = __reduce_add_sync(kFull, hi);
         if (lane == 0)
-          *reinterpret_cast<uint4 *>(s_ctot + (size_t)c * G + 4 * q) =
+          *reinterpret_cast<uint4 *>(my_ctot + (size_t)c * G + 4 * q) =
               make_uint4(lo & 0xffffu, lo >> 16, hi & 0xffffu, hi >> 16);
       }
       // aggregate: this band's column counts, [128 cols][GQ] words
@@ -199,20 +265,24 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
   }
   __syncthreads();
 
-  // ---- horizontal carries: exclusive scans over warps and over chunks ----
-  for (int e = threadIdx.x; e < nrows * G; e += blockDim.x) {
+  // ---- horizontal carries: exclusive scans over the warps of each bin
+  // group (row carries) and over chunks (band counts left of each chunk) ----
+  const int ngl = min(f.gpc, f.ngroups - gs * f.gpc);  // bin groups in this item
+  for (int e = threadIdx.x; e < ngl * nrows * G; e += blockDim.x) {
+    const int l = e / (nrows * G), r = e - l * (nrows * G);
     uint32_t run = 0u;
-    for (int ww = 0; ww < NW; ++ww) {
-      uint32_t *p = s_row + (size_t)ww * f.R * G + e;
+    for (int ww = 0; ww < f.wpg; ++ww) {
+      uint32_t *p = s_row + (size_t)(l * f.wpg + ww) * f.R * G + r;
       const uint32_t v = *p;
       *p = run;
       run += v;
     }
   }
-  for (int b = threadIdx.x; b < G; b += blockDim.x) {
+  for (int e = threadIdx.x; e < ngl * G; e += blockDim.x) {
+    const int l = e / G, b = e - l * G;
     uint32_t run = 0u;
     for (int c = 0; c < f.nchunks; ++c) {
-      uint32_t *p = s_ctot + (size_t)c * G + b;
+      uint32_t *p = s_ctot + ((size_t)l * f.nchunks + c) * G + b;
       const uint32_t v = *p;
       *p = run;
       run += v;
@@ -223,10 +293,11 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
   // ---- publish aggregates (all chunks first: they depend on no one) ----
   for (int cc = 0; cc < my_m; ++cc) {
     const int c = c_begin + cc;
-    if (lane < G) f.agg_left[(size_t)(ci0 + c) * G + lane] = s_ctot[(size_t)c * G + lane];
+    if (lane < G) f.agg_left[(size_t)(ci0 + c) * G + lane] = my_ctot[(size_t)c * G + lane];
     __threadfence();
     __syncwarp();
-    if (publish && lane == 0) st_release_gpu(f.flags + ci0 + c, (epoch << 2) | kStateAgg);
+    if (publish && lane == 0)
+      st_release_gpu(f.flags + ci0 + c, (epoch << 2) | (stage_ok ? kStateAgg : kStatePoison));
   }
 
   // ---- per chunk: look-back, publish inclusive row, emit ----
@@ -235,23 +306,23 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
     const unsigned int ci = ci0 + c;
     const int x = c * kChunk + 4 * lane;
 
-    uint32_t acc[G][4];   // becomes the running H of this lane's 4 columns
-    uint32_t left[G];     // band-count sums left of the chunk, from aggregates
+    uint32_t left[G];  // band-count sums left of the chunk, from aggregates
     uint32_t s16[GQ][4][2];
 #pragma unroll
-    for (int b = 0; b < G; ++b) {
-      left[b] = 0u;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) acc[b][i] = 0u;
-    }
+    for (int b = 0; b < G; ++b) left[b] = 0u;
 #pragma unroll
     for (int q = 0; q < GQ; ++q)
 #pragma unroll
       for (int i = 0; i < 4; ++i) s16[q][i][0] = s16[q][i][1] = 0u;
 
-    bool poisoned = false;
+    bool poisoned = !stage_ok;
     bool summed = false;
-    for (int j = k - 1; j >= 0; --j) {
+    int incl_at = -1;  // band whose inclusive row ends the look-back
+    // Look back over the bands above, nearest first: add each band's
+    // aggregate until one has published its inclusive row (measured faster
+    // than polling a 32-band window per warp, which costs 32 acquire loads
+    // when the band just above has usually published already).
+    for (int j = k - 1; j >= 0 && !poisoned; --j) {
       const unsigned int cj = ((unsigned)j * f.ngroups + g) * (unsigned)f.nchunks + c;
       const uint32_t st = wait_flag(f.flags + cj, epoch, ctrl, timeout_ns);
       if (st == kStatePoison) {
@@ -259,11 +330,7 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
         break;
       }
       if (st == kStateIncl) {
-#pragma unroll
-        for (int b = 0; b < G; ++b) {
-          const uint4 v = ld_relaxed_v4(f.incl + ((size_t)cj * G + b) * kChunk + 4 * lane);
-          acc[b][0] = v.x; acc[b][1] = v.y; acc[b][2] = v.z; acc[b][3] = v.w;
-        }
+        incl_at = j;
         break;
       }
       // aggregate: add the band's column counts (16-bit lanes, at most H)
@@ -274,24 +341,43 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
         const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          const int q = (4 * jj + t) % GQ, i = (4 * jj + t) / GQ;
-          s16[q][i][0] += __byte_perm(wv[t], 0u, 0x4140u);
-          s16[q][i][1] += __byte_perm(wv[t], 0u, 0x4342u);
+          const int q = (4 * jj + t) % GQ, ii = (4 * jj + t) / GQ;
+          s16[q][ii][0] += __byte_perm(wv[t], 0u, 0x4140u);
+          s16[q][ii][1] += __byte_perm(wv[t], 0u, 0x4342u);
         }
       }
 #pragma unroll
       for (int b4 = 0; b4 < GQ; ++b4) {
         const uint4 v = ld_relaxed_v4(f.agg_left + (size_t)cj * G + 4 * b4);
-        left[4 * b4 + 0] += v.x; left[4 * b4 + 1] += v.y;
-        left[4 * b4 + 2] += v.z; left[4 * b4 + 3] += v.w;
+        left[4 * b4 + 0] += v.x;
+        left[4 * b4 + 1] += v.y;
+        left[4 * b4 + 2] += v.z;
+        left[4 * b4 + 3] += v.w;
       }
       summed = true;
     }
     poisoned = __any_sync(kFull, poisoned);
 
     if (!poisoned) {
-      // top = incl row found + sum over the aggregates passed (Eq. 1 split
-      // into the part left of the chunk and a prefix across the chunk)
+      // top = inclusive row found + the aggregates passed (Eq. 1 split into
+      // the count left of the chunk and a prefix across the chunk)
+      uint32_t acc[G][4];  // becomes the running H of this lane's 4 columns
+      if (incl_at >= 0) {
+        const unsigned int cj = ((unsigned)incl_at * f.ngroups + g) * (unsigned)f.nchunks + c;
+#pragma unroll
+        for (int b = 0; b < G; ++b) {
+          const uint4 v = ld_relaxed_v4(f.incl + ((size_t)cj * G + b) * kChunk + 4 * lane);
+          acc[b][0] = v.x;
+          acc[b][1] = v.y;
+          acc[b][2] = v.z;
+          acc[b][3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int b = 0; b < G; ++b)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[b][i] = 0u;
+      }
       if (summed) {
 #pragma unroll
         for (int b = 0; b < G; ++b) {
@@ -304,13 +390,16 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
           for (int i = 0; i < 4; ++i) acc[b][i] += v[i] + left[b];
         }
       }
-      // inclusive row of this band = top + own aggregate, published for the bands below
+      // inclusive row of this band = top + own aggregate, for the bands below
       const uint32_t *own = f.agg_cnt + ((size_t)ci * kChunk + 4 * lane) * GQ;
       uint32_t ow[4 * GQ];
 #pragma unroll
       for (int jj = 0; jj < GQ; ++jj) {
         const uint4 v = *reinterpret_cast<const uint4 *>(own + 4 * jj);
-        ow[4 * jj + 0] = v.x; ow[4 * jj + 1] = v.y; ow[4 * jj + 2] = v.z; ow[4 * jj + 3] = v.w;
+        ow[4 * jj + 0] = v.x;
+        ow[4 * jj + 1] = v.y;
+        ow[4 * jj + 2] = v.z;
+        ow[4 * jj + 3] = v.w;
       }
 #pragma unroll
       for (int b = 0; b < G; ++b) {
@@ -319,7 +408,7 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
 #pragma unroll
         for (int i = 0; i < 4; ++i) v[i] = __byte_perm(ow[i * GQ + q], 0u, 0x4440u + bb);
         chunk_scan32(v, lane);
-        const uint32_t lown = s_ctot[(size_t)c * G + b];
+        const uint32_t lown = my_ctot[(size_t)c * G + b];
         if (publish)
           *reinterpret_cast<uint4 *>(f.incl + ((size_t)ci * G + b) * kChunk + 4 * lane) =
               make_uint4(acc[b][0] + v[0] + lown, acc[b][1] + v[1] + lown,
@@ -330,22 +419,22 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
       if (publish && lane == 0) st_release_gpu(f.flags + ci, (epoch << 2) | kStateIncl);
 
       // ---- emit the band's rows of this chunk ----
-      uint32_t *rowc = s_row + (size_t)w * f.R * G;
-      const uint8_t *row = f.in + (long long)y0 * f.pitch;
-      uint32_t un[4];
-      load_offsets<VEC>(row, x, f.W, nbins, gbase, un);
-      for (int yl = 0; yl < nrows; ++yl) {
-        uint32_t u[4] = {un[0], un[1], un[2], un[3]};
-        if (yl + 1 < nrows)
-          load_offsets<VEC>(row + (long long)(yl + 1) * f.pitch, x, f.W, nbins, gbase, un);
-        uint32_t rc[G];
-#pragma unroll
-        for (int b4 = 0; b4 < GQ; ++b4) {
-          const uint4 v = *reinterpret_cast<const uint4 *>(rowc + (size_t)yl * G + 4 * b4);
-          rc[4 * b4 + 0] = v.x; rc[4 * b4 + 1] = v.y; rc[4 * b4 + 2] = v.z; rc[4 * b4 + 3] = v.w;
+      if (staged != c) {
+        if (!stage_tile<TMA>(f, tmap, tile, bar, phase, y0, nrows, c, lane, timeout_ns)) {
+          if (lane == 0) latch_status(ctrl, kStatusTimeout);
+          continue;
         }
+        staged = c;
+      }
+      const size_t plane = (size_t)f.H * (size_t)f.W;
+      const bool last_chunk = (cc == my_m - 1);  // its row carries are not needed again
+      for (int yl = 0; yl < nrows; ++yl) {
+        uint32_t u[4];
+        tile_offsets(tile, yl, lane, x, f.W, nbins, gbase, u);
+        uint32_t *rcp = myrow + (size_t)yl * G;
 #pragma unroll
         for (int q = 0; q < GQ; ++q) {
+          uint4 rc = *reinterpret_cast<const uint4 *>(rcp + 4 * q);
           uint32_t p[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) p[i] = shl_clamp(1u, u[i] - 32u * q);
@@ -359,23 +448,29 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
           p[1] += ex;
           p[2] += ex;
           p[3] = t;
+          const uint32_t rcv[4] = {rc.x, rc.y, rc.z, rc.w};
 #pragma unroll
           for (int bb = 0; bb < 4; ++bb) {
-            const int b = 4 * q + bb;
             const uint32_t sel = 0x4440u + bb;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[b][i] += __byte_perm(p[i], 0u, sel) + rc[b];
-            rc[b] += __byte_perm(tot, 0u, sel);
+            for (int i = 0; i < 4; ++i) acc[4 * q + bb][i] += __byte_perm(p[i], 0u, sel) + rcv[bb];
+          }
+          if (!last_chunk) {
+            rc.x += __byte_perm(tot, 0u, 0x4440u);
+            rc.y += __byte_perm(tot, 0u, 0x4441u);
+            rc.z += __byte_perm(tot, 0u, 0x4442u);
+            rc.w += __byte_perm(tot, 0u, 0x4443u);
+            __syncwarp();
+            if (lane == 0) *reinterpret_cast<uint4 *>(rcp + 4 * q) = rc;
           }
         }
         // store the row: bin-major H[b][y][x..x+3] or pixel-major H[y][x+i][b]
         const int y = y0 + yl;
         if (f.layout == 0) {
+          uint32_t *o = f.out + ((size_t)(g * G) * f.H + y) * f.W + x;
 #pragma unroll
-          for (int b = 0; b < G; ++b) {
-            const int bg = g * G + b;
-            if (bg < f.B) {
-              uint32_t *o = f.out + ((size_t)bg * f.H + y) * f.W + x;
+          for (int b = 0; b < G; ++b, o += plane) {
+            if (g * G + b < f.B) {
               if (VEC) {
                 if (x < f.W) st_stream_v4(o, acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
               } else {
@@ -390,29 +485,24 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
           for (int i = 0; i < 4; ++i) {
             if (x + i < f.W) {
               uint32_t *o = f.out + ((size_t)y * f.W + x + i) * f.B + g * G;
-              if (VEC && (f.B % G == 0)) {
 #pragma unroll
-                for (int b4 = 0; b4 < GQ; ++b4)
+              for (int b4 = 0; b4 < GQ; ++b4) {
+                if (VEC && (f.B & 3) == 0 && g * G + 4 * b4 + 4 <= f.B) {
                   st_stream_v4(o + 4 * b4, acc[4 * b4][i], acc[4 * b4 + 1][i], acc[4 * b4 + 2][i],
                                acc[4 * b4 + 3][i]);
-              } else {
+                } else {
 #pragma unroll
-                for (int b = 0; b < G; ++b)
-                  if (g * G + b < f.B) st_stream(o + b, acc[b][i]);
+                  for (int bb = 0; bb < 4; ++bb)
+                    if (g * G + 4 * b4 + bb < f.B) st_stream(o + 4 * b4 + bb, acc[4 * b4 + bb][i]);
+                }
               }
             }
           }
         }
-        __syncwarp();
-        if (lane == 0) {
-#pragma unroll
-          for (int b4 = 0; b4 < GQ; ++b4)
-            *reinterpret_cast<uint4 *>(rowc + (size_t)yl * G + 4 * b4) =
-                make_uint4(rc[4 * b4], rc[4 * b4 + 1], rc[4 * b4 + 2], rc[4 * b4 + 3]);
-        }
       }
     } else {
       if (publish && lane == 0) st_release_gpu(f.flags + ci, (epoch << 2) | kStatePoison);
+      if (!stage_ok && lane == 0) latch_status(ctrl, kStatusTimeout);
     }
   }
 }
@@ -422,14 +512,25 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, unsigned int it
 // belongs to a CTA that is already running; the last CTA to finish resets
 // the ticket and advances the epoch, so launches need no host-side reset
 // and can be captured in a CUDA graph.
-template <int G, int MMAX, bool VEC>
-__global__ void __launch_bounds__(512) scan_kernel(FrameDesc f, Ctrl *ctrl,
-                                                    unsigned long long timeout_ns) {
-  extern __shared__ __align__(16) uint32_t smem[];
+template <int G, int MMAX, bool TMA, bool VEC>
+__global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
+    scan_kernel(FrameDesc f, const __grid_constant__ CUtensorMap tmap, Ctrl *ctrl,
+                unsigned long long timeout_ns) {
+  extern __shared__ uint8_t smem_raw[];
   __shared__ unsigned int s_item, s_epoch;
-  uint32_t *s_row = smem;
-  uint32_t *s_ctot = smem + (size_t)(blockDim.x >> 5) * f.R * G;
+  const int NW = blockDim.x >> 5;
+  const SmemLayout L = smem_layout(NW, f.R, G, f.nchunks * f.gpc);
+  uint8_t *base = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint8_t *s_tiles = base + L.tile_off;
+  uint32_t *s_row = reinterpret_cast<uint32_t *>(base + L.row_off);
+  uint32_t *s_ctot = reinterpret_cast<uint32_t *>(base + L.ctot_off);
+  uint64_t *s_bar = reinterpret_cast<uint64_t *>(base + L.bar_off);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (TMA && lane == 0) mbar_init(s_bar + w, 1);
   if (threadIdx.x == 0) s_epoch = *(volatile unsigned int *)&ctrl->epoch & 0x3fffffffu;
+  if (TMA) mbar_init_fence();
+  uint32_t phase = 0;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(&ctrl->ticket, 1u);
     __syncthreads();
@@ -437,7 +538,78 @@ __global__ void __launch_bounds__(512) scan_kernel(FrameDesc f, Ctrl *ctrl,
     const uint32_t epoch = s_epoch;
     __syncthreads();
     if (it >= f.nitems) break;
-    process_item<G, MMAX, VEC>(f, it, epoch, ctrl, timeout_ns, s_row, s_ctot);
+    process_item<G, MMAX, TMA, VEC>(f, &tmap, it, epoch, ctrl, timeout_ns, s_tiles, s_row, s_ctot,
+                                    s_bar, phase);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int d = atomicAdd(&ctrl->done, 1u);
+    if (d == gridDim.x - 1) {
+      ctrl->ticket = 0u;
+      ctrl->done = 0u;
+      __threadfence();
+      atomicAdd(&ctrl->epoch, 1u);
+    }
+  }
+}
+
+// Batched persistent kernel: one launch over the work items of many frames
+// of uneven size (Sec. 4.4's image sequences, as one work-list).  Tickets
+// run frame by frame and band-major within a frame, so a CTA only waits on
+// bands of its own frame that a running CTA holds.  Per-frame descriptors
+// and TMA tensor maps live in device memory; shared memory is sized for the
+// largest frame (R_max rows, nchunk_gpc_max chunk x group columns).
+template <int G, int MMAX, bool TMA, bool VEC>
+__global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
+    batch_kernel(const FrameDesc *frames, const CUtensorMap *__restrict__ tmaps,
+                 const unsigned int *item_end, int nframes, int R_max,
+                 int nchunk_gpc_max, Ctrl *ctrl, unsigned long long timeout_ns) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ unsigned int s_item, s_epoch;
+  __shared__ int s_frame;
+  __shared__ __align__(16) FrameDesc s_f;
+  const int NW = blockDim.x >> 5;
+  const SmemLayout L = smem_layout(NW, R_max, G, nchunk_gpc_max);
+  uint8_t *base = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint8_t *s_tiles = base + L.tile_off;
+  uint32_t *s_row = reinterpret_cast<uint32_t *>(base + L.row_off);
+  uint32_t *s_ctot = reinterpret_cast<uint32_t *>(base + L.ctot_off);
+  uint64_t *s_bar = reinterpret_cast<uint64_t *>(base + L.bar_off);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (TMA && lane == 0) mbar_init(s_bar + w, 1);
+  if (threadIdx.x == 0) s_epoch = *(volatile unsigned int *)&ctrl->epoch & 0x3fffffffu;
+  if (TMA) mbar_init_fence();
+  const unsigned int total = ld_relaxed_u32(item_end + nframes - 1);
+  uint32_t phase = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned int t = atomicAdd(&ctrl->ticket, 1u);
+      s_item = t;
+      int lo = 0, hi = nframes - 1;  // first frame whose item range ends after t
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ld_relaxed_u32(item_end + mid) > t) hi = mid; else lo = mid + 1;
+      }
+      s_frame = lo;
+    }
+    __syncthreads();
+    const unsigned int t = s_item;
+    const int fi = s_frame;
+    const uint32_t epoch = s_epoch;
+    if (t < total) {
+      // descriptors are read with coherent loads (never a stale cached line)
+      constexpr int kWords = (int)(sizeof(FrameDesc) / sizeof(uint32_t));
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(frames + fi);
+      for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+        reinterpret_cast<uint32_t *>(&s_f)[i] = ld_relaxed_u32(src + i);
+    }
+    __syncthreads();
+    if (t >= total) break;
+    const unsigned int it = t - (fi > 0 ? ld_relaxed_u32(item_end + fi - 1) : 0u);
+    process_item<G, MMAX, TMA, VEC>(s_f, tmaps + fi, it, epoch, ctrl, timeout_ns, s_tiles, s_row,
+                                    s_ctot, s_bar, phase);
     __syncthreads();
   }
   if (threadIdx.x == 0) {

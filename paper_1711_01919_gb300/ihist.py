@@ -31,7 +31,9 @@ IHIST_PIXEL_MAJOR = 1
 EXPORTED = (
     "ihist_plan", "ihist_plan_tuned", "ihist_plan_get_tune", "ihist_workspace_bytes",
     "ihist_output_bytes", "ihist_compute", "ihist_query", "ihist_sequence_host", "ihist_status",
-    "ihist_destroy", "ihist_error_string",
+    "ihist_destroy", "ihist_error_string", "ihist_batch_plan", "ihist_batch_set_io",
+    "ihist_batch_compute", "ihist_batch_query", "ihist_batch_status", "ihist_batch_workspace_bytes",
+    "ihist_batch_items", "ihist_batch_destroy", "ihist_batch_query_all", "ihist_batch_upload_compute",
 )
 
 
@@ -49,12 +51,25 @@ class ihist_tune_t(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int),
         ("timeout_us", ctypes.c_uint),
         ("fault_skip_band", ctypes.c_int),
-        ("reserved", ctypes.c_int * 4),
+        ("groups_per_cta", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
+    ]
+
+
+class ihist_frame_t(ctypes.Structure):
+    _fields_ = [
+        ("h", ctypes.c_int),
+        ("w", ctypes.c_int),
+        ("nbins", ctypes.c_int),
+        ("layout", ctypes.c_int),
+        ("d_in", ctypes.c_void_p),
+        ("in_pitch", ctypes.c_size_t),
+        ("d_out", ctypes.c_void_p),
     ]
 
 
 TUNE_FIELDS = ("rows_per_band", "bins_per_cta", "chunks_per_warp", "ctas_per_sm", "timeout_us",
-               "fault_skip_band")
+               "fault_skip_band", "groups_per_cta")
 
 _lock = threading.Lock()
 _lib = None
@@ -91,6 +106,27 @@ def load(path: str = LIB_PATH):
         L.ihist_status.restype = ci
         L.ihist_destroy.argtypes = [vp]
         L.ihist_destroy.restype = None
+        fp = ctypes.POINTER(ihist_frame_t)
+        L.ihist_batch_plan.argtypes = [fp, ci, ctypes.POINTER(ihist_tune_t), ctypes.POINTER(vp)]
+        L.ihist_batch_plan.restype = ci
+        L.ihist_batch_set_io.argtypes = [vp, fp, ci, vp]
+        L.ihist_batch_set_io.restype = ci
+        L.ihist_batch_compute.argtypes = [vp, vp]
+        L.ihist_batch_compute.restype = ci
+        L.ihist_batch_query.argtypes = [vp, ci, vp, vp, ci, vp, vp]
+        L.ihist_batch_query.restype = ci
+        L.ihist_batch_query_all.argtypes = [vp, vp, ci, vp, vp]
+        L.ihist_batch_query_all.restype = ci
+        L.ihist_batch_upload_compute.argtypes = [vp, ctypes.POINTER(vp), vp, vp]
+        L.ihist_batch_upload_compute.restype = ci
+        L.ihist_batch_status.argtypes = [vp, vp, ctypes.POINTER(ci)]
+        L.ihist_batch_status.restype = ci
+        L.ihist_batch_workspace_bytes.argtypes = [vp]
+        L.ihist_batch_workspace_bytes.restype = sz
+        L.ihist_batch_items.argtypes = [vp]
+        L.ihist_batch_items.restype = cu
+        L.ihist_batch_destroy.argtypes = [vp]
+        L.ihist_batch_destroy.restype = None
         L.ihist_error_string.argtypes = [ci]
         L.ihist_error_string.restype = ctypes.c_char_p
         _lib = L
@@ -171,6 +207,68 @@ def ihist_destroy(plan: int) -> None:
         load().ihist_destroy(plan)
 
 
+def _frames_array(frames):
+    arr = (ihist_frame_t * len(frames))()
+    for i, fr in enumerate(frames):
+        h, w, nbins, layout, d_in, pitch, d_out = fr
+        arr[i] = ihist_frame_t(h, w, nbins, layout, d_in, pitch, d_out)
+    return arr
+
+
+def ihist_batch_plan(frames, tune=None) -> int:
+    """frames: sequence of (h, w, nbins, layout, d_in, in_pitch, d_out)."""
+    arr = _frames_array(frames)
+    out = ctypes.c_void_p()
+    t = _tune_struct(tune) if tune else None
+    _check(load().ihist_batch_plan(arr, len(frames), ctypes.byref(t) if t else None, ctypes.byref(out)),
+           "ihist_batch_plan")
+    return out.value
+
+
+def ihist_batch_set_io(batch: int, frames, stream: int = 0) -> None:
+    arr = _frames_array(frames)
+    _check(load().ihist_batch_set_io(batch, arr, len(frames), stream), "ihist_batch_set_io")
+
+
+def ihist_batch_compute(batch: int, stream: int = 0) -> None:
+    _check(load().ihist_batch_compute(batch, stream), "ihist_batch_compute")
+
+
+def ihist_batch_query(batch: int, frame: int, d_hist: int, d_rects: int, n: int, d_hist_out: int,
+                      stream: int = 0) -> None:
+    _check(load().ihist_batch_query(batch, frame, d_hist, d_rects, n, d_hist_out, stream),
+           "ihist_batch_query")
+
+
+def ihist_batch_query_all(batch: int, d_rects: int, n: int, d_out: int, stream: int = 0) -> None:
+    _check(load().ihist_batch_query_all(batch, d_rects, n, d_out, stream), "ihist_batch_query_all")
+
+
+def ihist_batch_upload_compute(batch: int, h_frames, stream: int = 0, copy_stream: int = 0) -> None:
+    """h_frames: host addresses (ints) of the batch's frames, page-locked."""
+    arr = (ctypes.c_void_p * len(h_frames))(*h_frames)
+    _check(load().ihist_batch_upload_compute(batch, arr, stream, copy_stream), "ihist_batch_upload_compute")
+
+
+def ihist_batch_status(batch: int, stream: int = 0) -> int:
+    st = ctypes.c_int(-1)
+    _check(load().ihist_batch_status(batch, stream, ctypes.byref(st)), "ihist_batch_status")
+    return st.value
+
+
+def ihist_batch_workspace_bytes(batch: int) -> int:
+    return int(load().ihist_batch_workspace_bytes(batch))
+
+
+def ihist_batch_items(batch: int) -> int:
+    return int(load().ihist_batch_items(batch))
+
+
+def ihist_batch_destroy(batch: int) -> None:
+    if batch:
+        load().ihist_batch_destroy(batch)
+
+
 # --------------------------------------------------------------- torch glue
 
 def _stream(stream):
@@ -239,6 +337,90 @@ class Plan:
     def close(self):
         if self.handle:
             ihist_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def out_shape(h: int, w: int, nbins: int, layout: int):
+    return (nbins, h, w) if layout == IHIST_BIN_MAJOR else (h, w, nbins)
+
+
+class Batch:
+    """Many frames (CUDA uint8 [h][w] tensors, any mix of shapes) in one
+    persistent launch; outputs are int32 tensors holding uint32 counts."""
+
+    def __init__(self, frames, nbins, layouts=None, outs=None, tune=None):
+        import torch
+        n = len(frames)
+        nb = list(nbins) if hasattr(nbins, "__len__") else [nbins] * n
+        ly = list(layouts) if layouts is not None else [IHIST_BIN_MAJOR] * n
+        self.frames = list(frames)
+        self.nbins, self.layouts = nb, ly
+        self.outs = list(outs) if outs is not None else [
+            torch.empty(out_shape(f.shape[0], f.shape[1], b, l), dtype=torch.int32, device=f.device)
+            for f, b, l in zip(self.frames, nb, ly)]
+        self.handle = ihist_batch_plan(self._desc(), tune)
+
+    def _desc(self):
+        d = []
+        for f, b, l, o in zip(self.frames, self.nbins, self.layouts, self.outs):
+            if f.dtype.itemsize != 1 or f.dim() != 2 or f.stride(1) != 1:
+                raise ValueError("frames must be 2-D uint8 tensors with unit column stride")
+            d.append((f.shape[0], f.shape[1], b, l, f.data_ptr(), f.stride(0), o.data_ptr()))
+        return d
+
+    def set_io(self, frames, outs, stream=None):
+        self.frames, self.outs = list(frames), list(outs)
+        ihist_batch_set_io(self.handle, self._desc(), _stream(stream))
+
+    def compute(self, stream=None):
+        ihist_batch_compute(self.handle, _stream(stream))
+        return self.outs
+
+    def query(self, i, rects, out=None, stream=None):
+        import torch
+        n = rects.shape[0]
+        if out is None:
+            out = torch.empty((n, self.nbins[i]), dtype=torch.int32, device=rects.device)
+        ihist_batch_query(self.handle, i, self.outs[i].data_ptr(), rects.data_ptr(), n, out.data_ptr(),
+                          _stream(stream))
+        return out
+
+    def query_all(self, rects, out=None, stream=None):
+        """rects: CUDA int32 [nframes][n][4] -> int32 [n * sum(nbins)] (frame-major rows)."""
+        import torch
+        n = rects.shape[1]
+        if out is None:
+            out = torch.empty((n * sum(self.nbins),), dtype=torch.int32, device=rects.device)
+        ihist_batch_query_all(self.handle, rects.data_ptr(), n, out.data_ptr(), _stream(stream))
+        return out
+
+    def upload_compute(self, h_frames, stream=None, copy_stream=None):
+        """Copy page-locked host frames (CPU uint8 tensors) in on copy_stream, then compute."""
+        ihist_batch_upload_compute(self.handle, [f.data_ptr() for f in h_frames], _stream(stream),
+                                   _stream(copy_stream))
+        return self.outs
+
+    def status(self, stream=None) -> int:
+        return ihist_batch_status(self.handle, _stream(stream))
+
+    def items(self) -> int:
+        return ihist_batch_items(self.handle)
+
+    def close(self):
+        if self.handle:
+            ihist_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

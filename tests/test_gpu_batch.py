@@ -1,0 +1,161 @@
+"""Batched persistent launch over frames of uneven size: every frame's result
+equals the oracle (and the single-frame path) word for word."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_01919_gb300 import ihist, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1711_01919_gb300 import build as cuda_build
+    cuda_build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def ref_layout(img, nbins, layout):
+    ref = oracle.integral_histogram(img, nbins)
+    return ref if layout == 0 else np.ascontiguousarray(ref.transpose(1, 2, 0))
+
+
+def check_batch(batch, imgs, nbins, layouts):
+    for i, (img, b, l) in enumerate(zip(imgs, nbins, layouts)):
+        got = u32(batch.outs[i]).reshape(ihist.out_shape(img.shape[0], img.shape[1], b, l))
+        ref = ref_layout(img, b, l)
+        assert np.array_equal(got, ref), "frame %d (%dx%d B=%d layout %d): %d words differ" % (
+            i, img.shape[0], img.shape[1], b, l, int((got != ref).sum()))
+
+
+MIXED = [(1, 1, 1, 0), (5, 3, 3, 1), (37, 131, 16, 0), (240, 320, 16, 0), (64, 257, 7, 1),
+         (480, 640, 32, 0), (100, 1000, 64, 1), (720, 1280, 64, 0), (33, 2049, 100, 0),
+         (300, 4096, 8, 0), (17, 128, 256, 1)]
+
+
+@pytest.mark.parametrize("tune", [None, {"rows_per_band": 8}, {"rows_per_band": 64, "bins_per_cta": 8},
+                                  {"rows_per_band": 3, "ctas_per_sm": 1}])
+def test_mixed_batch(tune):
+    imgs = [synth.uniform_frame(1000 + i, h, w) for i, (h, w, b, l) in enumerate(MIXED)]
+    nbins = [b for (h, w, b, l) in MIXED]
+    layouts = [l for (h, w, b, l) in MIXED]
+    with ihist.Batch([torch.from_numpy(x).cuda() for x in imgs], nbins, layouts, tune=tune) as batch:
+        batch.compute()
+        assert batch.status() == ihist.IHIST_OK
+        check_batch(batch, imgs, nbins, layouts)
+
+
+def test_unaligned_frames_take_the_plain_path():
+    imgs = [synth.uniform_frame(7 + i, 90, 300) for i in range(3)]
+    dev = []
+    for i, img in enumerate(imgs):
+        buf = torch.zeros(1 + 90 * 311 + 16, dtype=torch.uint8, device="cuda")
+        v = buf[1:1 + 90 * 311].view(90, 311)[:, :300]
+        v.copy_(torch.from_numpy(img))
+        dev.append(v)
+    with ihist.Batch(dev, [12, 5, 64], [0, 1, 0]) as batch:
+        batch.compute()
+        assert batch.status() == ihist.IHIST_OK
+        check_batch(batch, imgs, [12, 5, 64], [0, 1, 0])
+
+
+def test_uneven_batch_workload_256_frames():
+    # 256 frames, resolutions {320x240, 640x480, 1280x720, 1920x1080}, B in {16, 32, 64}
+    specs = synth.uneven_batch_specs(synth.workload_seed(3), 256)
+    imgs = [synth.uniform_frame(s, h, w) for (h, w, b, s) in specs]
+    nbins = [b for (h, w, b, s) in specs]
+    with ihist.Batch([torch.from_numpy(x).cuda() for x in imgs], nbins) as batch:
+        batch.compute()
+        assert batch.status() == ihist.IHIST_OK
+        for i in range(len(imgs)):
+            got = u32(batch.outs[i]).reshape(nbins[i], imgs[i].shape[0], imgs[i].shape[1])
+            assert np.array_equal(got, oracle.integral_histogram(imgs[i], nbins[i])), "frame %d" % i
+        # the same frames through single-frame plans give the same words
+        for i in (0, 1, 2):
+            with ihist.Plan(imgs[i].shape[0], imgs[i].shape[1], nbins[i]) as p:
+                assert torch.equal(p.compute(batch.frames[i]), batch.outs[i])
+
+
+def test_graph_replay_and_set_io():
+    shapes = [(200, 700, 24), (64, 128, 8), (480, 640, 32)]
+    a = [synth.uniform_frame(50 + i, h, w) for i, (h, w, b) in enumerate(shapes)]
+    b_ = [synth.gradient_frame(60 + i, h, w) for i, (h, w, b) in enumerate(shapes)]
+    nb = [b for (h, w, b) in shapes]
+    da = [torch.from_numpy(x).cuda() for x in a]
+    db = [torch.from_numpy(x).cuda() for x in b_]
+    with ihist.Batch(da, nb) as batch:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            batch.compute(stream=s)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            batch.compute(stream=s)
+        for _ in range(2):
+            for o in batch.outs:
+                o.fill_(-1)
+            g.replay()
+            torch.cuda.synchronize()
+            check_batch(batch, a, nb, [0, 0, 0])
+        outs2 = [torch.empty_like(o) for o in batch.outs]
+        batch.set_io(db, outs2)
+        batch.compute()
+        assert batch.status() == ihist.IHIST_OK
+        check_batch(batch, b_, nb, [0, 0, 0])
+        q = batch.query(2, torch.from_numpy(synth.rects(3, 50, 480, 640)).cuda())
+        ref = oracle.query(oracle.integral_histogram(b_[2], 32), synth.rects(3, 50, 480, 640))
+        assert np.array_equal(u32(q), ref)
+
+
+def test_batch_rejects_bad_frames():
+    d = torch.zeros((10, 10), dtype=torch.uint8, device="cuda")
+    o = torch.zeros((4, 10, 10), dtype=torch.int32, device="cuda")
+    with pytest.raises(ihist.IhistError):
+        ihist.ihist_batch_plan([(10, 10, 0, 0, d.data_ptr(), 10, o.data_ptr())])
+    with pytest.raises(ihist.IhistError):
+        ihist.ihist_batch_plan([(10, 10, 4, 0, d.data_ptr(), 5, o.data_ptr())])
+    with pytest.raises(ihist.IhistError):
+        ihist.ihist_batch_plan([])
+
+
+def test_query_all_over_a_mixed_batch():
+    shapes = [(37, 131, 16, 0), (240, 320, 7, 1), (5, 3, 3, 0), (100, 1000, 64, 1)]
+    imgs = [synth.uniform_frame(300 + i, h, w) for i, (h, w, b, l) in enumerate(shapes)]
+    nb = [b for (h, w, b, l) in shapes]
+    ly = [l for (h, w, b, l) in shapes]
+    n = 40
+    rects = np.stack([synth.rects(400 + i, n, h, w) for i, (h, w, b, l) in enumerate(shapes)])
+    rects[1, 5] = (0, 0, 320, 3)   # out of range: zero row and BAD_RECT
+    with ihist.Batch([torch.from_numpy(x).cuda() for x in imgs], nb, ly) as batch:
+        batch.compute()
+        q = u32(batch.query_all(torch.from_numpy(rects).cuda()))
+        assert batch.status() == ihist.IHIST_ERR_BAD_RECT
+        off = 0
+        for i, (img, b) in enumerate(zip(imgs, nb)):
+            got = q[off:off + n * b].reshape(n, b)
+            ref = oracle.query(oracle.integral_histogram(img, b), rects[i])
+            assert np.array_equal(got, ref), "frame %d" % i
+            off += n * b
+        assert not q[n * nb[0] + 5 * nb[1]: n * nb[0] + 6 * nb[1]].any()
+
+
+def test_upload_compute_from_pinned_host_frames():
+    shapes = [(120, 500, 24), (64, 256, 8), (90, 640, 32)]
+    nb = [b for (h, w, b) in shapes]
+    d_in = [torch.empty((h, w), dtype=torch.uint8, device="cuda") for (h, w, b) in shapes]
+    with ihist.Batch(d_in, nb) as batch:
+        copy = torch.cuda.Stream()
+        for rep in range(3):
+            imgs = [synth.gradient_frame(500 + 10 * rep + i, h, w) for i, (h, w, b) in enumerate(shapes)]
+            host = [torch.from_numpy(x).pin_memory() for x in imgs]
+            batch.upload_compute(host, copy_stream=copy)
+            torch.cuda.synchronize()
+            assert batch.status() == ihist.IHIST_OK
+            check_batch(batch, imgs, nb, [0, 0, 0])

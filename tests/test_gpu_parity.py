@@ -84,7 +84,7 @@ TUNINGS = [
     {"rows_per_band": 1},
     {"rows_per_band": 3, "bins_per_cta": 4},
     {"rows_per_band": 7, "bins_per_cta": 16},
-    {"rows_per_band": 255, "bins_per_cta": 8},
+    {"rows_per_band": 255, "bins_per_cta": 8, "chunks_per_warp": 4},
     {"rows_per_band": 16, "chunks_per_warp": 2},
     {"rows_per_band": 5, "chunks_per_warp": 4, "bins_per_cta": 4},
     {"rows_per_band": 9, "chunks_per_warp": 8, "bins_per_cta": 8},
@@ -100,6 +100,28 @@ def test_tilings(tune):
         img = synth.uniform_frame(h + w + nbins, h, w)
         ref = oracle.integral_histogram(img, nbins)
         assert_same(run_gpu(img, nbins, tune=tune), ref, "%s %dx%d B=%d" % (tune, h, w, nbins))
+
+
+@pytest.mark.parametrize("h,w,nbins,tune", [
+    (300, 640, 24, {"groups_per_cta": 3, "rows_per_band": 11}),
+    (300, 384, 40, {"groups_per_cta": 5, "rows_per_band": 7}),
+    (100, 130, 44, {"groups_per_cta": 7, "rows_per_band": 9}),      # last group set partial
+    (61, 1000, 30, {"groups_per_cta": 2, "chunks_per_warp": 2, "rows_per_band": 5}),
+    (40, 256, 64, {"groups_per_cta": 4, "bins_per_cta": 8, "rows_per_band": 3}),
+])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_multi_group_ctas(h, w, nbins, tune, layout):
+    img = synth.uniform_frame(h * w + nbins, h, w)
+    ref = oracle.integral_histogram(img, nbins)
+    got = run_gpu(img, nbins, layout=layout, tune=tune)
+    assert_same(got, to_layout(ref, layout), "%s %dx%d B=%d" % (tune, h, w, nbins))
+
+
+def test_infeasible_tiling_is_rejected():
+    # 8 warps x 255 rows x 128 bytes of staged input exceed shared memory
+    with pytest.raises(ihist.IhistError) as e:
+        ihist.Plan(300, 1000, 24, 0, tune={"rows_per_band": 255, "bins_per_cta": 8, "chunks_per_warp": 1})
+    assert e.value.code == ihist.IHIST_ERR_UNSUPPORTED
 
 
 def test_pitch_and_unaligned_input():
