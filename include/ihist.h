@@ -212,6 +212,34 @@ unsigned int ihist_batch_items(ihist_batch_t batch);
 /* Release the batch (NULL is a no-op); no launch of it may still be running. */
 void ihist_batch_destroy(ihist_batch_t batch);
 
+/* ---- Integral histogram without any device allocation -----------------
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc (code running inside a host callback or an
+ * allocator hook, under a memory pool that must not grow, or in a process
+ * whose device allocations belong to a framework the caller cannot reach).
+ * It computes exactly what ihist_plan + ihist_compute compute (same kernel,
+ * same words) for one frame, but takes its carry scratch from a fixed
+ * 8 MiB array inside the library image instead of a plan.
+ *   - Allocates nothing: no cudaMalloc, no cudaFree, no plan.
+ *   - The scratch exists once per device, for as long as the process keeps
+ *     the library loaded (8 MiB of every device that loads it).
+ *   - The first call on a device sets that device up (looks up the device
+ *     address of the scratch and the kernels' shared-memory limits) with
+ *     the device current; make that first call before any stream capture.
+ *   - All calls share the scratch, which keeps the previous call's
+ *     contents; each call clears the parts that must start at zero on its
+ *     stream.  Calls whose work may overlap on the GPU (other streams, other
+ *     host threads) race on the scratch: keep them on one stream.
+ *   - A frame whose carries do not fit the scratch returns
+ *     IHIST_ERR_UNSUPPORTED (roughly: up to 1920 x 1080 with 64 bins fits;
+ *     8192 x 8192 with 128 bins does not -- use a plan there).
+ * Arguments as for ihist_plan / ihist_compute.  device_status: NULL for a
+ * fully asynchronous call; otherwise the call waits for the stream and
+ * stores the device status (IHIST_OK or IHIST_ERR_LOOKBACK_TIMEOUT). */
+int ihist_compute_noalloc(int h, int w, int nbins, int layout, const uint8_t *d_in,
+                          size_t in_pitch, uint32_t *d_out, void *stream, int *device_status);
+
 /* Synchronise the stream, then read and clear the plan's device status word
  * into *device_status (IHIST_OK if no device error was latched since the
  * last read).  Returns IHIST_OK or a host/CUDA error code. */

@@ -34,6 +34,7 @@ EXPORTED = (
     "ihist_destroy", "ihist_error_string", "ihist_batch_plan", "ihist_batch_set_io",
     "ihist_batch_compute", "ihist_batch_query", "ihist_batch_status", "ihist_batch_workspace_bytes",
     "ihist_batch_items", "ihist_batch_destroy", "ihist_batch_query_all", "ihist_batch_upload_compute",
+    "ihist_compute_noalloc",
 )
 
 
@@ -127,6 +128,8 @@ def load(path: str = LIB_PATH):
         L.ihist_batch_items.restype = cu
         L.ihist_batch_destroy.argtypes = [vp]
         L.ihist_batch_destroy.restype = None
+        L.ihist_compute_noalloc.argtypes = [ci, ci, ci, ci, vp, sz, vp, vp, ctypes.POINTER(ci)]
+        L.ihist_compute_noalloc.restype = ci
         L.ihist_error_string.argtypes = [ci]
         L.ihist_error_string.restype = ctypes.c_char_p
         _lib = L
@@ -194,6 +197,16 @@ def ihist_sequence_host(plan: int, h_frames: int, frame_stride: int, nframes: in
     _check(load().ihist_sequence_host(plan, h_frames, frame_stride, nframes, d_slots, d_outs, nouts,
                                       d_rects, nrects, d_query, h_query_out, stream, copy_stream),
            "ihist_sequence_host")
+
+
+def ihist_compute_noalloc(h: int, w: int, nbins: int, layout: int, d_in: int, in_pitch: int, d_out: int,
+                          stream: int = 0, wait: bool = True):
+    """Integral histogram with no device allocation (fixed scratch in the
+    library); returns the device status when wait is true, else None."""
+    st = ctypes.c_int(-1)
+    _check(load().ihist_compute_noalloc(h, w, nbins, layout, d_in, in_pitch, d_out, stream,
+                                        ctypes.byref(st) if wait else None), "ihist_compute_noalloc")
+    return st.value if wait else None
 
 
 def ihist_status(plan: int, stream: int = 0) -> int:
