@@ -164,19 +164,29 @@ typedef struct {
   uint32_t *d_out;
 } ihist_frame_t;
 
-/* Plan a batch of n >= 1 frames (limits per frame as for ihist_plan).  tune
- * may be NULL; its bins_per_cta (4 or 8) and rows_per_band apply to every
- * frame, chunks_per_warp and groups_per_cta are chosen per frame to fill
- * a CTA of up to 16 warps.  Allocates the batch's device workspace. */
+/* Plan a batch of n >= 1 frames (limits per frame as for ihist_plan); the
+ * frames also fix the capacity of the batch's n slots (see
+ * ihist_batch_set_io).  tune may be NULL; its bins_per_cta (4 or 8) and
+ * rows_per_band apply to every frame; chunks per warp and groups per CTA
+ * are chosen per frame to fill a CTA of up to 16 warps.  Frames bound
+ * later by ihist_batch_set_io keep within the launch shape the planned
+ * frames fixed (chunks per warp, carry width per CTA), which may leave some
+ * of a narrower frame's CTA idle.  Allocates the batch's device workspace
+ * and pinned staging buffers. */
 int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_tune_t *tune,
                      ihist_batch_t *out);
 
-/* Point the batch's frames at new buffers (shapes, bin counts and layouts
- * must equal the planned ones).  The new descriptors are copied on `stream`,
- * so later launches on that stream see them. */
+/* Bind the batch to n frames (1 <= n <= the planned count), for example a
+ * new set of requests.  Frame i takes slot i, whose carry workspace was
+ * sized for the i-th planned frame: any frame fits whose carries are no
+ * larger (same or smaller height, width and bin count always do);
+ * otherwise IHIST_ERR_UNSUPPORTED and the previous binding stays.  The new
+ * descriptors are copied on `stream`, so later launches on it see them; the
+ * call may wait for this batch's previous descriptor copy to finish.
+ * Nothing is allocated. */
 int ihist_batch_set_io(ihist_batch_t batch, const ihist_frame_t *frames, int n, void *stream);
 
-/* Compute every frame of the batch in one launch on `stream`. */
+/* Compute every bound frame of the batch in one launch on `stream`. */
 int ihist_batch_compute(ihist_batch_t batch, void *stream);
 
 /* Region histograms (Eq. 2) on frame `frame` of the batch; arguments as for

@@ -1,0 +1,200 @@
+"""Autotuner: pick the scan kernel's tiling (and, if allowed, the layout) by
+measurement, cached per device and frame shape.
+
+Search space (ihist_tune_t fields): rows per band R, bins per CTA G (4 or
+8), 128-column chunks per warp m, bin groups per CTA.  Each candidate is
+timed with CUDA events on a seeded uniform frame (median of a few launches
+after warm-up); candidates the library rejects (shared memory, registers)
+are skipped.  For a batch the search covers R and G of the batched launch.
+``choose_layout`` times compute plus a query load for bin-major and
+pixel-major output and keeps the faster, for callers that accept either.
+
+Results are cached in a JSON file (``IHIST_TUNE_CACHE`` or
+``~/.cache/ihist_tune.json``) keyed by device name and shape.  The timing
+function is injectable, so the search and cache logic run on the CPU in the
+tests.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+import threading
+
+from . import ihist, synth
+
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("IHIST_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "ihist_tune.json")
+
+
+def _load_cache(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(path, cache):
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + ".%d.tmp" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def plan_candidates(h: int, w: int, nbins: int):
+    """Tilings worth timing for one frame shape (the default first)."""
+    nchunks = -(-w // 128)
+    out = [{}]
+    for G in (4, 8):
+        for m in (1, 2, 4, 8):
+            wpg = -(-nchunks // m)
+            if wpg > 16 or (m > 1 and -(-nchunks // (m // 2)) <= 16 and nchunks <= 16):
+                continue  # needs more than 16 warps, or a smaller m already fits
+            ngroups = -(-nbins // G)
+            for gpc in sorted({1, min(ngroups, max(1, 16 // wpg))}):
+                for R in (0, 16, 24, 32, 48, 64):
+                    if R and R > h:
+                        continue
+                    t = {"bins_per_cta": G, "chunks_per_warp": m, "groups_per_cta": gpc}
+                    if R:
+                        t["rows_per_band"] = R
+                    out.append(t)
+    return out
+
+
+def batch_candidates():
+    return [{}] + [{"bins_per_cta": G, "rows_per_band": R} for G in (4, 8) for R in (16, 24, 32, 40, 48, 64)]
+
+
+def _device_key():
+    import torch
+    return torch.cuda.get_device_name()
+
+
+def time_plan(h, w, nbins, layout, tune, reps=5):
+    """Median ms of ihist_compute with this tiling (raises IhistError if rejected)."""
+    import torch
+    frame = torch.from_numpy(synth.uniform_frame(12345, h, w)).cuda()
+    with ihist.Plan(h, w, nbins, layout, tune=tune or None) as plan:
+        out = plan.empty_output()
+        for _ in range(2):
+            plan.compute(frame, out)
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.compute(frame, out)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        if plan.status() != ihist.IHIST_OK:
+            raise RuntimeError("device status error while tuning")
+    return statistics.median(ms)
+
+
+def time_batch(shapes, tune, reps=3):
+    """Median ms of one batched launch over frames of these (h, w, nbins, layout)."""
+    import torch
+    frames = [torch.from_numpy(synth.uniform_frame(100 + i, h, w)).cuda() for i, (h, w, b, l) in enumerate(shapes)]
+    with ihist.Batch(frames, [s[2] for s in shapes], [s[3] for s in shapes], tune=tune or None) as batch:
+        for _ in range(2):
+            batch.compute()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            batch.compute()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        if batch.status() != ihist.IHIST_OK:
+            raise RuntimeError("device status error while tuning")
+    return statistics.median(ms)
+
+
+def _search(cands, timer):
+    best, best_ms, tried = None, float("inf"), []
+    for t in cands:
+        try:
+            ms = timer(t)
+        except ihist.IhistError:
+            continue
+        tried.append((ms, t))
+        if ms < best_ms:
+            best, best_ms = t, ms
+    if best is None:
+        raise RuntimeError("no tiling candidate ran")
+    return best, best_ms, tried
+
+
+def tune_plan(h, w, nbins, layout=ihist.IHIST_BIN_MAJOR, timer=None, device=None, use_cache=True):
+    """Best tiling for ihist_plan_tuned on this device and shape."""
+    device = device or _device_key()
+    key = "plan|%s|%dx%dx%d|%d" % (device, h, w, nbins, layout)
+    path = cache_path()
+    with _lock:
+        cache = _load_cache(path) if use_cache else {}
+        if key in cache:
+            return cache[key]["tune"]
+    timer = timer or (lambda t: time_plan(h, w, nbins, layout, t))
+    best, ms, _ = _search(plan_candidates(h, w, nbins), timer)
+    if use_cache:
+        with _lock:
+            cache = _load_cache(path)
+            cache[key] = {"tune": best, "ms": ms}
+            _store_cache(path, cache)
+    return best
+
+
+def tune_batch(shapes, timer=None, device=None, use_cache=True):
+    """Best (bins_per_cta, rows_per_band) for a batch of (h, w, nbins, layout) frames."""
+    device = device or _device_key()
+    sig = ",".join("%dx%dx%dx%d" % tuple(s) for s in sorted(set(tuple(s) for s in shapes)))
+    key = "batch|%s|%d|%s" % (device, len(shapes), sig)
+    path = cache_path()
+    with _lock:
+        cache = _load_cache(path) if use_cache else {}
+        if key in cache:
+            return cache[key]["tune"]
+    timer = timer or (lambda t: time_batch(shapes, t))
+    best, ms, _ = _search(batch_candidates(), timer)
+    if use_cache:
+        with _lock:
+            cache = _load_cache(path)
+            cache[key] = {"tune": best, "ms": ms}
+            _store_cache(path, cache)
+    return best
+
+
+def choose_layout(h, w, nbins, queries_per_frame=1000, timer=None):
+    """Bin-major or pixel-major for a frame that is computed once and then
+    queried `queries_per_frame` times: whichever takes less time in total."""
+    if timer is None:
+        import torch
+
+        def timer(layout):
+            frame = torch.from_numpy(synth.uniform_frame(77, h, w)).cuda()
+            rects = torch.from_numpy(synth.rects(78, max(1, queries_per_frame), h, w)).cuda()
+            with ihist.Plan(h, w, nbins, layout) as plan:
+                out = plan.empty_output()
+                for _ in range(2):
+                    plan.compute(frame, out)
+                    if queries_per_frame:
+                        plan.query(out, rects)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(3):
+                    plan.compute(frame, out)
+                    if queries_per_frame:
+                        plan.query(out, rects)
+                b.record()
+                torch.cuda.synchronize()
+                return a.elapsed_time(b) / 3
+    t_bm = timer(ihist.IHIST_BIN_MAJOR)
+    t_pm = timer(ihist.IHIST_PIXEL_MAJOR)
+    return ihist.IHIST_PIXEL_MAJOR if t_pm < t_bm else ihist.IHIST_BIN_MAJOR

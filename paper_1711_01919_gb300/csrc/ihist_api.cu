@@ -499,23 +499,36 @@ extern "C" void ihist_destroy(ihist_plan_t p) {
 }
 
 // ---------------------------------------------------------------- batches
+//
+// A batch plan owns `cap` frame slots.  Slot i's carry workspace is sized
+// for the frame it was planned with; ihist_batch_set_io may later bind any
+// n <= cap frames whose tilings fit their slots (same or smaller carries,
+// rows per band and width), so one plan serves a stream of changing
+// batches without allocating.  Every kernel variant (TMA / plain input,
+// 16-byte / scalar output) is prepared at plan time and the launch picks
+// the one the current frames allow.
 
 namespace {
 
-constexpr int kBatchWarps = 16;     // warps per CTA of the batched kernel
-constexpr int kBatchDefaultRows = 32;
+constexpr int kBatchWarps = 16;  // warps per CTA of the batched kernel
 
 // Per-frame tiling inside a 16-warp CTA: the chunks-per-warp m (1, 2 or 4)
 // and bin groups per CTA that keep the most warps busy, smaller m on ties.
-void batch_frame_tiling(int h, int w, int nbins, int G, int R_req, FrameDesc *f) {
+// Tiling of one frame in a batched launch: m chunks per warp (at most max_m)
+// and gpc bin groups per CTA, nchunks * gpc at most max_ncg (the per-CTA
+// carry width the launch's shared memory was sized for), maximising the
+// share of the CTA's 16 warps x m chunk slots that hold columns.
+void batch_frame_tiling(int h, int w, int nbins, int layout, int G, int R_req, int max_m, int max_ncg,
+                        FrameDesc *f) {
   const int nchunks = (w + kChunk - 1) / kChunk;
   const int ngroups = (nbins + G - 1) / G;
   double best = -1.0;
   int bm = 1, bwpg = nchunks, bgpc = 1;
-  for (int m = 1; m <= 4; m <<= 1) {
+  for (int m = 1; m <= max_m; m <<= 1) {
     const int wpg = (nchunks + m - 1) / m;
     if (wpg > kBatchWarps) continue;
-    const int gpc = std::max(1, std::min(ngroups, kBatchWarps / wpg));
+    const int gpc = std::min(std::min(ngroups, kBatchWarps / wpg), max_ncg / nchunks);
+    if (gpc < 1) continue;
     const double util = (double)nchunks * gpc / ((double)kBatchWarps * m);
     if (util > best + 1e-9) {
       best = util;
@@ -524,10 +537,12 @@ void batch_frame_tiling(int h, int w, int nbins, int G, int R_req, FrameDesc *f)
       bgpc = gpc;
     }
   }
+  std::memset(f, 0, sizeof(*f));
   f->H = h;
   f->W = w;
   f->B = nbins;
-  f->R = std::min(R_req > 0 ? R_req : kBatchDefaultRows, h);
+  f->layout = layout;
+  f->R = std::min(R_req, h);
   f->nbands = (h + f->R - 1) / f->R;
   f->ngroups = ngroups;
   f->nchunks = nchunks;
@@ -538,6 +553,8 @@ void batch_frame_tiling(int h, int w, int nbins, int G, int R_req, FrameDesc *f)
   f->nitems = (unsigned int)f->nbands * (unsigned int)f->ngsets;
   f->fault_skip_band = -1;
 }
+
+size_t frame_nci(const FrameDesc &f) { return (size_t)f.nbands * f.ngroups * f.nchunks; }
 
 bool frame_tma_ok(const ihist_frame_t &fr) {
   return !((uintptr_t)fr.d_in & 15u) && !(fr.in_pitch & 15u) && fr.w >= kChunk &&
@@ -551,24 +568,27 @@ bool frame_vec_ok(const ihist_frame_t &fr) {
 }  // namespace
 
 struct ihist_batch_s {
-  int device, sms, n, G, mmax, R_max, ncg_max, ctas_per_sm;
-  bool tma, vec;
+  int device, sms, cap, n, G, mmax, R_req, R_max, ncg_max, ctas_cap;
+  int ctas_per_sm[2][2];  // occupancy of each (tma, vec) variant
+  bool tma, vec;          // variant the current frames allow
   unsigned int timeout_us, total;
   size_t smem_bytes, ws_bytes;
+  unsigned long long bins_total;
   void *ws;
   Ctrl *ctrl;
   FrameDesc *d_fd;
   CUtensorMap *d_tm;
-  unsigned int *d_end;
-  std::vector<FrameDesc> fd;
+  unsigned int *d_end, *d_bins_end;
+  std::vector<size_t> slot_nci;                       // carry capacity of each slot
+  std::vector<uint32_t *> slot_flags, slot_cnt, slot_left, slot_incl;
+  std::vector<FrameDesc> fd;                          // current frames
   std::vector<ihist_frame_t> io;
-  FrameDesc *h_fd;     // pinned staging for set_io
-  CUtensorMap *h_tm;   // pinned staging for set_io
-  cudaEvent_t staged;  // last staging copy done
-  cudaEvent_t uploaded, computed;  // upload/compute pipeline
-  unsigned int *d_bins_end;        // prefix sums of bin counts (queries)
-  unsigned long long bins_total;
-  bool launched;                   // a compute has been enqueued
+  FrameDesc *h_fd;           // pinned staging
+  CUtensorMap *h_tm;
+  unsigned int *h_end, *h_bins_end;
+  cudaEvent_t staged;        // last staging copy done
+  cudaEvent_t uploaded, computed;
+  bool launched;
 };
 
 static bool encode_frame_map(const ihist_frame_t &fr, int R, CUtensorMap *map) {
@@ -583,28 +603,73 @@ static bool encode_frame_map(const ihist_frame_t &fr, int R, CUtensorMap *map) {
              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Fill the host copies of descriptors and tensor maps for the given I/O.
-static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames) {
-  for (int i = 0; i < b->n; ++i) {
+// Tile the given frames into the plan's slots and fill the pinned staging
+// copies (descriptors, tensor maps, item and bin prefix sums).  Nothing is
+// committed to b->fd / b->io unless every frame fits.
+static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames, int n) {
+  if (n < 1 || n > b->cap) return IHIST_ERR_INVALID_ARG;
+  std::vector<FrameDesc> fd(n);
+  bool tma = true, vec = true;
+  unsigned long long total = 0, bsum = 0;
+  for (int i = 0; i < n; ++i) {
     const ihist_frame_t &fr = frames[i];
-    FrameDesc &f = b->fd[i];
-    if (fr.h != f.H || fr.w != f.W || fr.nbins != f.B || fr.layout != f.layout)
+    int rc = validate_shape(fr.h, fr.w, fr.nbins, fr.layout);
+    if (rc != IHIST_OK) return rc;
+    if (!fr.d_in || !fr.d_out || fr.in_pitch < (size_t)fr.w || ((uintptr_t)fr.d_out & 3u) ||
+        fr.in_pitch > (size_t)LLONG_MAX)
       return IHIST_ERR_INVALID_ARG;
-    if (!fr.d_in || !fr.d_out || fr.in_pitch < (size_t)fr.w || ((uintptr_t)fr.d_out & 3u))
-      return IHIST_ERR_INVALID_ARG;
-    if (b->tma && !frame_tma_ok(fr)) return IHIST_ERR_INVALID_ARG;
-    if (b->vec && !frame_vec_ok(fr)) return IHIST_ERR_INVALID_ARG;
+    FrameDesc &f = fd[i];
+    batch_frame_tiling(fr.h, fr.w, fr.nbins, fr.layout, b->G, b->R_req, b->mmax, b->ncg_max, &f);
+    if (frame_nci(f) > b->slot_nci[i] || f.R > b->R_max || f.nchunks * f.gpc > b->ncg_max ||
+        mmax_for(f.m) > b->mmax)
+      return IHIST_ERR_UNSUPPORTED;  // does not fit the slot planned for it
     f.in = fr.d_in;
     f.pitch = (long long)fr.in_pitch;
     f.out = fr.d_out;
-    b->io[i] = fr;
-    b->h_fd[i] = f;
-    if (b->tma) {
-      if (!encode_frame_map(fr, f.R, &b->h_tm[i])) return IHIST_ERR_CUDA;
+    f.flags = b->slot_flags[i];
+    f.agg_cnt = b->slot_cnt[i];
+    f.agg_left = b->slot_left[i];
+    f.incl = b->slot_incl[i];
+    tma = tma && frame_tma_ok(fr);
+    vec = vec && frame_vec_ok(fr);
+    total += f.nitems;
+    bsum += (unsigned long long)fr.nbins;
+  }
+  if (total >= 0xffffffffull) return IHIST_ERR_UNSUPPORTED;
+  for (int i = 0; i < n; ++i) {
+    if (tma) {
+      if (!encode_frame_map(frames[i], fd[i].R, &b->h_tm[i])) return IHIST_ERR_CUDA;
     } else {
       std::memset(&b->h_tm[i], 0, sizeof(CUtensorMap));
     }
   }
+  unsigned long long run = 0, brun = 0;
+  for (int i = 0; i < n; ++i) {
+    run += fd[i].nitems;
+    brun += (unsigned long long)frames[i].nbins;
+    b->h_end[i] = (unsigned int)run;
+    b->h_bins_end[i] = (unsigned int)brun;
+    b->h_fd[i] = fd[i];
+  }
+  b->fd.assign(fd.begin(), fd.end());
+  b->io.assign(frames, frames + n);
+  b->n = n;
+  b->tma = tma;
+  b->vec = vec;
+  b->total = (unsigned int)total;
+  b->bins_total = bsum;
+  return IHIST_OK;
+}
+
+static int batch_upload(ihist_batch_s *b, cudaStream_t s) {
+  const int n = b->n;
+  if (cudaMemcpyAsync(b->d_fd, b->h_fd, (size_t)n * sizeof(FrameDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_tm, b->h_tm, (size_t)n * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_end, b->h_end, (size_t)n * sizeof(unsigned int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_bins_end, b->h_bins_end, (size_t)n * sizeof(unsigned int), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaEventRecord(b->staged, s) != cudaSuccess)
+    return IHIST_ERR_CUDA;
   return IHIST_OK;
 }
 
@@ -613,11 +678,14 @@ extern "C" void ihist_batch_destroy(ihist_batch_t b) {
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != b->device) cudaSetDevice(b->device);
+  if (b->staged) cudaEventSynchronize(b->staged);
   if (b->staged) cudaEventDestroy(b->staged);
   if (b->uploaded) cudaEventDestroy(b->uploaded);
   if (b->computed) cudaEventDestroy(b->computed);
   if (b->h_fd) cudaFreeHost(b->h_fd);
   if (b->h_tm) cudaFreeHost(b->h_tm);
+  if (b->h_end) cudaFreeHost(b->h_end);
+  if (b->h_bins_end) cudaFreeHost(b->h_bins_end);
   if (b->ws) cudaFree(b->ws);
   if (prev != b->device && prev >= 0) cudaSetDevice(prev);
   delete b;
@@ -637,98 +705,112 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
     const int rc = validate_shape(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout);
     if (rc != IHIST_OK) return rc;
   }
-  int dev = 0, sms = 0, optin = 0;
+  int dev = 0, sms = 0, optin = 0, smem_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return IHIST_ERR_CUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
     return IHIST_ERR_CUDA;
 
   ihist_batch_s *b = new (std::nothrow) ihist_batch_s();
   if (!b) return IHIST_ERR_OOM;
   b->device = dev;
   b->sms = sms;
-  b->n = n;
+  b->cap = n;
   b->G = t.bins_per_cta;
   b->timeout_us = t.timeout_us ? t.timeout_us : kDefaultTimeoutUs;
-  b->fd.resize(n);
-  b->io.resize(n);
-  b->tma = true;
-  b->vec = true;
-  int mmax = 1;
-  std::vector<unsigned int> ends(n);
-  unsigned long long total = 0;
-  size_t nci_total = 0;
-  // default rows per band: the largest R (at most 64) whose shared memory
-  // (16 warps x R rows of staged input and row carries) fits two CTAs per SM
-  int R_req = t.rows_per_band;
-  if (R_req == 0) {
-    int smem_sm = 0;
-    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
-      delete b;
-      return IHIST_ERR_CUDA;
-    }
-    int ncg = 1;
-    for (int i = 0; i < n; ++i) ncg = std::max(ncg, (frames[i].w + kChunk - 1) / kChunk * 16);
-    R_req = 8;
-    for (int r = 64; r >= 8; --r)
-      if (2 * (smem_layout(kBatchWarps, r, b->G, ncg).bytes + 1024) <= (size_t)smem_sm) {
-        R_req = r;
+  // every kernel variant the batch may launch may use the opt-in shared memory
+  for (int mm = 1; mm <= 4; mm <<= 1)
+    for (int tma = 0; tma < 2; ++tma)
+      for (int vec = 0; vec < 2; ++vec) {
+        BatchFn fn = batch_fn(b->G, mm, tma != 0, vec != 0);
+        cudaFuncAttributes a;
+        if (!fn || cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
+          cudaGetLastError();
+          delete b;
+          return fn ? IHIST_ERR_CUDA : IHIST_ERR_UNSUPPORTED;
+        }
+        const size_t dyn_max = (size_t)optin > a.sharedSizeBytes ? (size_t)optin - a.sharedSizeBytes : 0;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max) != cudaSuccess) {
+          cudaGetLastError();
+          delete b;
+          return IHIST_ERR_CUDA;
+        }
+      }
+  // default rows per band: the largest R (at most 64) at which the kernel
+  // still keeps two CTAs per SM (16 warps x R rows of staged input and row
+  // carries in shared memory), as the occupancy calculator reports it
+  b->R_req = t.rows_per_band;
+  if (b->R_req == 0) {
+    b->R_req = 8;
+    for (int r = 64; r >= 8; --r) {
+      int rmax = 1, ncg = 1, mm = 1;
+      for (int i = 0; i < n; ++i) {
+        FrameDesc f;
+        batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, r, 4, INT_MAX,
+                           &f);
+        rmax = std::max(rmax, f.R);
+        ncg = std::max(ncg, f.nchunks * f.gpc);
+        mm = std::max(mm, f.m);
+      }
+      int occ = 0;
+      const size_t smem = smem_layout(kBatchWarps, rmax, b->G, ncg).bytes;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_fn(b->G, mmax_for(mm), true, true),
+                                                        kBatchWarps * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        occ = 0;
+      }
+      if (occ >= 2) {
+        b->R_req = r;
         break;
       }
+    }
   }
+  // slot capacities from the planned frames
+  std::vector<FrameDesc> plan_fd(n);
+  int mm = 1;
+  size_t nci_total = 0;
   for (int i = 0; i < n; ++i) {
-    FrameDesc &f = b->fd[i];
-    std::memset(&f, 0, sizeof(f));
-    batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, b->G, R_req, &f);
-    f.layout = frames[i].layout;
-    mmax = std::max(mmax, f.m);
-    b->R_max = std::max(b->R_max, f.R);
-    b->ncg_max = std::max(b->ncg_max, f.nchunks * f.gpc);
-    total += f.nitems;
-    ends[i] = (unsigned int)total;
-    nci_total += (size_t)f.nbands * f.ngroups * f.nchunks;
-    b->tma = b->tma && frame_tma_ok(frames[i]);
-    b->vec = b->vec && frame_vec_ok(frames[i]);
+    batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, b->R_req, 4,
+                       INT_MAX, &plan_fd[i]);
+    mm = std::max(mm, plan_fd[i].m);
+    b->R_max = std::max(b->R_max, plan_fd[i].R);
+    b->ncg_max = std::max(b->ncg_max, plan_fd[i].nchunks * plan_fd[i].gpc);
+    b->slot_nci.push_back(frame_nci(plan_fd[i]));
+    nci_total += frame_nci(plan_fd[i]);
   }
-  if (total >= 0xffffffffull) {
-    delete b;
-    return IHIST_ERR_UNSUPPORTED;
-  }
-  b->total = (unsigned int)total;
-  b->mmax = mmax_for(mmax);
-  BatchFn fn = batch_fn(b->G, b->mmax, b->tma, b->vec);
-  if (!fn) {
-    delete b;
-    return IHIST_ERR_UNSUPPORTED;
-  }
-  cudaFuncAttributes a;
-  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
-    cudaGetLastError();
-    delete b;
-    return IHIST_ERR_CUDA;
-  }
-  const size_t dyn_max = (size_t)optin > a.sharedSizeBytes ? (size_t)optin - a.sharedSizeBytes : 0;
+  b->mmax = mmax_for(mm);
   b->smem_bytes = smem_layout(kBatchWarps, b->R_max, b->G, b->ncg_max).bytes;
-  if (b->smem_bytes > dyn_max ||
-      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max) != cudaSuccess) {
-    cudaGetLastError();
-    delete b;
-    return IHIST_ERR_UNSUPPORTED;
-  }
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBatchWarps * 32, b->smem_bytes) !=
-          cudaSuccess ||
-      occ < 1) {
-    cudaGetLastError();
-    delete b;
-    return IHIST_ERR_UNSUPPORTED;
-  }
-  b->ctas_per_sm = t.ctas_per_sm > 0 ? std::min(t.ctas_per_sm, occ) : occ;
+  for (int tma = 0; tma < 2; ++tma)
+    for (int vec = 0; vec < 2; ++vec) {
+      BatchFn fn = batch_fn(b->G, b->mmax, tma != 0, vec != 0);
+      cudaFuncAttributes a;
+      if (!fn || cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fn ? IHIST_ERR_CUDA : IHIST_ERR_UNSUPPORTED;
+      }
+      const size_t dyn_max = (size_t)optin > a.sharedSizeBytes ? (size_t)optin - a.sharedSizeBytes : 0;
+      int occ = 0;
+      if (b->smem_bytes > dyn_max ||
+          cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBatchWarps * 32, b->smem_bytes) != cudaSuccess ||
+          occ < 1) {
+        cudaGetLastError();
+        delete b;
+        return IHIST_ERR_UNSUPPORTED;
+      }
+      b->ctas_per_sm[tma][vec] = t.ctas_per_sm > 0 ? std::min(t.ctas_per_sm, occ) : occ;
+    }
 
-  // workspace: control, descriptors, tensor maps, item ends, then per-frame carries
+  // workspace: control block and flags (cleared), descriptor arrays
+  // (written only by copies), then each slot's carries
   size_t off = 0;
   const size_t o_ctrl = off;
   off = align_up(off + sizeof(Ctrl), 256);
+  const size_t o_flags = off;
+  off = align_up(off + nci_total * sizeof(uint32_t), 256);
+  const size_t zero_end = off;
   const size_t o_fd = off;
   off = align_up(off + (size_t)n * sizeof(FrameDesc), 256);
   const size_t o_tm = off;
@@ -737,13 +819,9 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   off = align_up(off + (size_t)n * sizeof(unsigned int), 256);
   const size_t o_bend = off;
   off = align_up(off + (size_t)n * sizeof(unsigned int), 256);
-  const size_t o_flags = off;
-  off = align_up(off + nci_total * sizeof(uint32_t), 256);
-  const size_t zero_bytes = off;
   const size_t o_carry = off;
   for (int i = 0; i < n; ++i) {
-    const FrameDesc &f = b->fd[i];
-    const size_t nci = (size_t)f.nbands * f.ngroups * f.nchunks;
+    const size_t nci = b->slot_nci[i];
     off = align_up(off + nci * kChunk * (b->G / 4) * 4, 256);
     off = align_up(off + nci * b->G * 4, 256);
     off = align_up(off + nci * b->G * kChunk * 4, 256);
@@ -752,6 +830,8 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   if (cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess ||
       cudaMallocHost((void **)&b->h_fd, (size_t)n * sizeof(FrameDesc)) != cudaSuccess ||
       cudaMallocHost((void **)&b->h_tm, (size_t)n * sizeof(CUtensorMap)) != cudaSuccess ||
+      cudaMallocHost((void **)&b->h_end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
+      cudaMallocHost((void **)&b->h_bins_end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->computed, cudaEventDisableTiming) != cudaSuccess) {
@@ -765,46 +845,32 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   b->d_tm = reinterpret_cast<CUtensorMap *>(base + o_tm);
   b->d_end = reinterpret_cast<unsigned int *>(base + o_end);
   b->d_bins_end = reinterpret_cast<unsigned int *>(base + o_bend);
-  std::vector<unsigned int> bins_end(n);
-  unsigned long long bsum = 0;
-  for (int i = 0; i < n; ++i) {
-    bsum += (unsigned long long)frames[i].nbins;
-    bins_end[i] = (unsigned int)bsum;
-  }
-  b->bins_total = bsum;
   size_t fo = o_flags, co = o_carry;
   for (int i = 0; i < n; ++i) {
-    FrameDesc &f = b->fd[i];
-    const size_t nci = (size_t)f.nbands * f.ngroups * f.nchunks;
-    f.flags = reinterpret_cast<uint32_t *>(base + fo);
+    const size_t nci = b->slot_nci[i];
+    b->slot_flags.push_back(reinterpret_cast<uint32_t *>(base + fo));
     fo += nci * sizeof(uint32_t);
-    f.agg_cnt = reinterpret_cast<uint32_t *>(base + co);
+    b->slot_cnt.push_back(reinterpret_cast<uint32_t *>(base + co));
     co = align_up(co + nci * kChunk * (b->G / 4) * 4, 256);
-    f.agg_left = reinterpret_cast<uint32_t *>(base + co);
+    b->slot_left.push_back(reinterpret_cast<uint32_t *>(base + co));
     co = align_up(co + nci * b->G * 4, 256);
-    f.incl = reinterpret_cast<uint32_t *>(base + co);
+    b->slot_incl.push_back(reinterpret_cast<uint32_t *>(base + co));
     co = align_up(co + nci * b->G * kChunk * 4, 256);
   }
-  int rc = batch_bind(b, frames);
+  int rc = batch_bind(b, frames, n);
   if (rc != IHIST_OK) {
     ihist_batch_destroy(b);
     return rc;
   }
-  // clear the control block and the flags only; the descriptor arrays
-  // between them are written once by the copies below
-  if (cudaMemset(b->ws, 0, sizeof(Ctrl)) != cudaSuccess ||
-      cudaMemset(base + o_flags, 0, zero_bytes - o_flags) != cudaSuccess ||
-      cudaMemcpy(b->d_fd, b->h_fd, (size_t)n * sizeof(FrameDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_tm, b->h_tm, (size_t)n * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_end, ends.data(), (size_t)n * sizeof(unsigned int), cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      cudaMemcpy(b->d_bins_end, bins_end.data(), (size_t)n * sizeof(unsigned int),
-                 cudaMemcpyHostToDevice) != cudaSuccess ||
+  // clear the control block and the flags only; the descriptor arrays are
+  // written once per binding by the copies
+  if (cudaMemset(b->ws, 0, zero_end) != cudaSuccess || batch_upload(b, 0) != IHIST_OK ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     ihist_batch_destroy(b);
     return IHIST_ERR_CUDA;
   }
+  (void)o_ctrl;
   *out = b;
   return IHIST_OK;
 }
@@ -816,25 +882,14 @@ static int check_batch_device(const ihist_batch_s *b) {
 }
 
 extern "C" int ihist_batch_set_io(ihist_batch_t b, const ihist_frame_t *frames, int n, void *stream) {
-  if (!b || !frames || n != b->n) return IHIST_ERR_INVALID_ARG;
+  if (!b || !frames) return IHIST_ERR_INVALID_ARG;
   int rc = check_batch_device(b);
   if (rc != IHIST_OK) return rc;
   // the staging buffers may still feed the previous copy
   if (cudaEventSynchronize(b->staged) != cudaSuccess) return IHIST_ERR_CUDA;
-  std::vector<ihist_frame_t> keep(b->io);
-  rc = batch_bind(b, frames);
-  if (rc != IHIST_OK) {
-    batch_bind(b, keep.data());
-    return rc;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemcpyAsync(b->d_fd, b->h_fd, (size_t)n * sizeof(FrameDesc), cudaMemcpyHostToDevice, s) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(b->d_tm, b->h_tm, (size_t)n * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s) !=
-          cudaSuccess ||
-      cudaEventRecord(b->staged, s) != cudaSuccess)
-    return IHIST_ERR_CUDA;
-  return IHIST_OK;
+  rc = batch_bind(b, frames, n);
+  if (rc != IHIST_OK) return rc;
+  return batch_upload(b, (cudaStream_t)stream);
 }
 
 extern "C" int ihist_batch_compute(ihist_batch_t b, void *stream) {
@@ -842,7 +897,8 @@ extern "C" int ihist_batch_compute(ihist_batch_t b, void *stream) {
   int rc = check_batch_device(b);
   if (rc != IHIST_OK) return rc;
   BatchFn fn = batch_fn(b->G, b->mmax, b->tma, b->vec);
-  const unsigned int grid = std::min<unsigned int>(b->total, (unsigned int)(b->ctas_per_sm * b->sms));
+  const int cps = b->ctas_per_sm[b->tma ? 1 : 0][b->vec ? 1 : 0];
+  const unsigned int grid = std::min<unsigned int>(b->total, (unsigned int)(cps * b->sms));
   const unsigned long long timeout_ns = (unsigned long long)b->timeout_us * 1000ull;
   fn<<<grid, kBatchWarps * 32, b->smem_bytes, (cudaStream_t)stream>>>(
       b->d_fd, b->d_tm, b->d_end, b->n, b->R_max, b->ncg_max, b->ctrl, timeout_ns);

@@ -301,7 +301,12 @@ class Plan:
     """
 
     def __init__(self, h: int, w: int, nbins: int, layout: int = IHIST_BIN_MAJOR, tune=None):
+        """tune: None (library defaults), a dict of ihist_tune_t fields, or
+        "auto" (measured by the autotuner, cached per device and shape)."""
         self.h, self.w, self.nbins, self.layout = h, w, nbins, layout
+        if tune == "auto":
+            from . import autotune
+            tune = autotune.tune_plan(h, w, nbins, layout)
         self.handle = (ihist_plan_tuned(h, w, nbins, layout, tune) if tune
                        else ihist_plan(h, w, nbins, layout))
         self.tune = ihist_plan_get_tune(self.handle)
@@ -383,7 +388,10 @@ class Batch:
         self.outs = list(outs) if outs is not None else [
             torch.empty(out_shape(f.shape[0], f.shape[1], b, l), dtype=torch.int32, device=f.device)
             for f, b, l in zip(self.frames, nb, ly)]
-        self.handle = ihist_batch_plan(self._desc(), tune)
+        if tune == "auto":
+            from . import autotune
+            tune = autotune.tune_batch([(f.shape[0], f.shape[1], b, l) for f, b, l in zip(self.frames, nb, ly)])
+        self.handle = ihist_batch_plan(self._desc(), tune or None)
 
     def _desc(self):
         d = []
@@ -393,9 +401,18 @@ class Batch:
             d.append((f.shape[0], f.shape[1], b, l, f.data_ptr(), f.stride(0), o.data_ptr()))
         return d
 
-    def set_io(self, frames, outs, stream=None):
-        self.frames, self.outs = list(frames), list(outs)
-        ihist_batch_set_io(self.handle, self._desc(), _stream(stream))
+    def set_io(self, frames, outs, nbins=None, layouts=None, stream=None):
+        """Bind new frames/outputs (any shapes that fit the planned slots)."""
+        frames, outs = list(frames), list(outs)
+        nb = list(nbins) if nbins is not None else self.nbins[:len(frames)]
+        ly = list(layouts) if layouts is not None else self.layouts[:len(frames)]
+        old = (self.frames, self.outs, self.nbins, self.layouts)
+        self.frames, self.outs, self.nbins, self.layouts = frames, outs, nb, ly
+        try:
+            ihist_batch_set_io(self.handle, self._desc(), _stream(stream))
+        except Exception:
+            self.frames, self.outs, self.nbins, self.layouts = old
+            raise
 
     def compute(self, stream=None):
         ihist_batch_compute(self.handle, _stream(stream))

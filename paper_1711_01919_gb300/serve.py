@@ -1,0 +1,441 @@
+"""Continuous-batching server for integral histograms.
+
+Requests arrive over time (Sec. 4.4's image sequences, served):
+
+* ``FrameRequest``  a uint8 frame and a bin count.  Its integral histogram
+  (Eq. 1) is computed on the GPU and then stays resident in device memory
+  for follow-up queries.  A frame is admitted only when its histogram
+  (h * w * nbins * 4 bytes) fits the HBM budget, after evicting the least
+  recently used resident histograms that no pending query holds.
+* ``QueryRequest``  rectangles whose region histograms (Eq. 2) are wanted
+  from a resident histogram.  The server picks the target among the
+  resident frames when the query is admitted (seeded, uniform) and holds it
+  until the query is answered; the rows are copied back to the host.
+
+The loop is continuous batching, not a queue: every iteration it admits
+what has arrived and fits, puts all admitted frames that are not yet
+running into ONE batched launch (``ihist_batch_upload_compute``: uploads on
+a copy stream, compute as soon as they land), so frames that arrive while
+a batch runs join the next one and their uploads overlap the running
+compute.  Queries whose histogram is ready are launched as they come.
+Latency is taken from GPU event timestamps against a reference event
+recorded at the start, so it does not depend on how often the host polls.
+
+``mode="plain"`` serves every frame with its own ``ihist_compute`` launch
+(no batching) -- the baseline the batched form is compared with.
+
+The GPU work sits behind ``GpuExecutor``; the admission, eviction and
+batching logic runs unchanged on a ``FakeExecutor`` in the CPU tests.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import heapq
+import time
+
+import numpy as np
+
+from . import synth
+
+
+@dataclasses.dataclass
+class FrameRequest:
+    rid: int
+    t_arrival: float          # seconds from the start of the run
+    h: int
+    w: int
+    nbins: int
+    frame: object = None      # host uint8 [h][w] (page-locked torch tensor on the GPU path)
+
+
+@dataclasses.dataclass
+class QueryRequest:
+    rid: int
+    t_arrival: float
+    rects: object             # int32 [n][4] host array
+    target: int = -1          # frame rid, chosen at admission
+
+
+@dataclasses.dataclass
+class Done:
+    rid: int
+    kind: str                 # "frame" or "query"
+    t_arrival: float
+    t_done: float
+    status: str = "ok"        # ok | rejected
+    target: int = -1
+
+
+def hist_bytes(h: int, w: int, nbins: int) -> int:
+    return h * w * nbins * 4
+
+
+class HistStore:
+    """Resident histograms under a byte budget; LRU over entries not pinned."""
+
+    def __init__(self, budget: int):
+        self.budget = budget
+        self.used = 0
+        self.entries = collections.OrderedDict()  # rid -> [bytes, pins, ready, payload]
+        self.evicted = 0
+
+    def can_fit(self, nbytes: int) -> bool:
+        if self.used + nbytes <= self.budget:
+            return True
+        free = sum(e[0] for e in self.entries.values() if e[1] == 0 and e[2])
+        return self.used - free + nbytes <= self.budget
+
+    def reserve(self, rid: int, nbytes: int, evict_cb=None) -> bool:
+        """Make room (evicting LRU unpinned ready entries) and reserve nbytes."""
+        if not self.can_fit(nbytes):
+            return False
+        for k in list(self.entries.keys()):
+            if self.used + nbytes <= self.budget:
+                break
+            e = self.entries[k]
+            if e[1] == 0 and e[2]:
+                self.used -= e[0]
+                del self.entries[k]
+                self.evicted += 1
+                if evict_cb:
+                    evict_cb(k, e[3])
+        if self.used + nbytes > self.budget:
+            return False
+        self.entries[rid] = [nbytes, 0, False, None]
+        self.used += nbytes
+        return True
+
+    def set_ready(self, rid: int, payload=None):
+        e = self.entries.get(rid)
+        if e is not None:
+            e[2] = True
+            if payload is not None:
+                e[3] = payload
+
+    def touch(self, rid: int):
+        if rid in self.entries:
+            self.entries.move_to_end(rid)
+
+    def pin(self, rid: int):
+        self.entries[rid][1] += 1
+        self.touch(rid)
+
+    def unpin(self, rid: int):
+        if rid in self.entries:
+            self.entries[rid][1] -= 1
+
+    def resident(self):
+        return list(self.entries.keys())
+
+    def payload(self, rid: int):
+        return self.entries[rid][3]
+
+    def ready(self, rid: int) -> bool:
+        return rid in self.entries and self.entries[rid][2]
+
+
+class FakeExecutor:
+    """CPU stand-in for the GPU: work finishes `latency` seconds after launch."""
+
+    def __init__(self, frame_latency=1e-4, query_latency=5e-5):
+        self.frame_latency, self.query_latency = frame_latency, query_latency
+        self.launches = []
+
+    def now(self):
+        return self._now
+
+    def launch_frames(self, reqs, t):
+        self.launches.append(("frames", [r.rid for r in reqs]))
+        return {"t": t + self.frame_latency, "payloads": {r.rid: ("hist", r.rid) for r in reqs}}
+
+    def launch_query(self, q, payload, t):
+        self.launches.append(("query", q.rid, q.target))
+        return {"t": t + self.query_latency, "result": ("rows", q.rid, payload)}
+
+    def poll(self, handle, t):
+        return t >= handle["t"]
+
+    def done_time(self, handle):
+        return handle["t"]
+
+    def release(self, rid, payload):
+        pass
+
+
+class Server:
+    """Continuous-batching request loop over an executor (see module doc)."""
+
+    def __init__(self, executor, budget_bytes: int, max_batch: int = 64, mode: str = "batched",
+                 seed: int = 4):
+        self.ex = executor
+        self.store = HistStore(budget_bytes)
+        self.max_batch = max_batch if mode == "batched" else 1
+        self.mode = mode
+        self.rng = np.random.default_rng(seed)
+        self.done = []
+        self.results = {}
+
+    def run(self, requests, clock, max_wall: float = 600.0):
+        """Serve `requests` (sorted by t_arrival).  clock() returns seconds since
+        the start; the loop ends when every request has completed."""
+        pending = collections.deque(requests)
+        admit_frames = collections.deque()   # arrived, waiting for budget
+        ready_frames = []                    # admitted, not launched
+        waiting_queries = collections.deque()
+        inflight = []                        # (handle, kind, payload)
+        arrived_frames = {}
+        t_start_wall = time.perf_counter()
+        while pending or admit_frames or ready_frames or waiting_queries or inflight:
+            if time.perf_counter() - t_start_wall > max_wall:
+                raise RuntimeError("serving loop exceeded %.0f s" % max_wall)
+            t = clock()
+            # 1. arrivals
+            while pending and pending[0].t_arrival <= t:
+                r = pending.popleft()
+                if isinstance(r, FrameRequest):
+                    admit_frames.append(r)
+                    arrived_frames[r.rid] = r
+                else:
+                    live = self.store.resident()
+                    if not live:
+                        self.done.append(Done(r.rid, "query", r.t_arrival, t, "rejected"))
+                        continue
+                    r.target = int(live[int(self.rng.integers(len(live)))])
+                    self.store.pin(r.target)
+                    waiting_queries.append(r)
+            # 2. admission by HBM footprint (FIFO)
+            while admit_frames:
+                r = admit_frames[0]
+                nb = hist_bytes(r.h, r.w, r.nbins)
+                if nb > self.store.budget:
+                    admit_frames.popleft()
+                    self.done.append(Done(r.rid, "frame", r.t_arrival, t, "rejected"))
+                    continue
+                if not self.store.reserve(r.rid, nb, self.ex.release):
+                    break
+                admit_frames.popleft()
+                ready_frames.append(r)
+            # 3. one batched launch of everything admitted (continuous batching)
+            while ready_frames:
+                batch, ready_frames = ready_frames[:self.max_batch], ready_frames[self.max_batch:]
+                h = self.ex.launch_frames(batch, t)
+                inflight.append((h, "frames", batch))
+                if self.mode != "batched":
+                    continue
+                break
+            # 4. queries whose histogram is ready
+            for _ in range(len(waiting_queries)):
+                q = waiting_queries.popleft()
+                if self.store.ready(q.target):
+                    h = self.ex.launch_query(q, self.store.payload(q.target), t)
+                    inflight.append((h, "query", q))
+                else:
+                    waiting_queries.append(q)
+            # 5. completions
+            still = []
+            for h, kind, obj in inflight:
+                if self.ex.poll(h, clock()):
+                    td = self.ex.done_time(h)
+                    if kind == "frames":
+                        for r in obj:
+                            self.store.set_ready(r.rid, h["payloads"][r.rid])
+                            self.store.touch(r.rid)
+                            self.done.append(Done(r.rid, "frame", r.t_arrival, td))
+                    else:
+                        self.store.unpin(obj.target)
+                        self.store.touch(obj.target)
+                        self.results[obj.rid] = h.get("result")
+                        self.done.append(Done(obj.rid, "query", obj.t_arrival, td, target=obj.target))
+                else:
+                    still.append((h, kind, obj))
+            inflight = still
+        return self.done
+
+    def report(self, wall_s: float):
+        out = {"mode": self.mode, "evicted": self.store.evicted}
+        for kind in ("frame", "query"):
+            ok = [d for d in self.done if d.kind == kind and d.status == "ok"]
+            lat = np.array([d.t_done - d.t_arrival for d in ok]) * 1e3
+            out[kind] = {
+                "completed": len(ok),
+                "rejected": sum(1 for d in self.done if d.kind == kind and d.status != "ok"),
+                "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                "max_ms": float(lat.max()) if len(lat) else None,
+                "per_s": len(ok) / wall_s if wall_s > 0 else None,
+            }
+        return out
+
+
+# ----------------------------------------------------------------- workload
+
+def serving_workload(seed: int, duration_s: float, frame_rate: float = 2000.0, query_rate: float = 200.0,
+                     rects_per_query: int = 10000, frame_pool=None):
+    """Poisson frame arrivals (mix of the uneven batch) and Poisson query
+    arrivals with `rects_per_query` random rectangles each.  frame_pool:
+    optional {(h, w): [frames]} of host frames to cycle through."""
+    ft = synth.poisson_arrivals(seed, frame_rate, duration_s)
+    qt = synth.poisson_arrivals(seed + 1, query_rate, duration_s)
+    specs = synth.uneven_batch_specs(seed + 2, len(ft))
+    reqs = []
+    use = collections.Counter()
+    for i, (t, (h, w, b, s)) in enumerate(zip(ft, specs)):
+        fr = None
+        if frame_pool is not None:
+            pool = frame_pool[(h, w)]
+            fr = pool[use[(h, w)] % len(pool)]
+            use[(h, w)] += 1
+        reqs.append(FrameRequest(i, float(t), h, w, b, fr))
+    n0 = len(reqs)
+    for j, t in enumerate(qt):
+        # rectangles in the smallest resolution of the mix, valid in every frame
+        reqs.append(QueryRequest(n0 + j, float(t), synth.rects(seed + 10 + j, rects_per_query, 240, 320)))
+    reqs.sort(key=lambda r: r.t_arrival)
+    return reqs
+
+
+# ----------------------------------------------------------------- the GPU
+
+class GpuExecutor:
+    """Runs the server's launches with libihist on one GPU.
+
+    batched: `nslots`-frame batch plans (two, alternating) whose slots are
+    sized for the largest frame of the mix; every launch rebinds the slots to
+    the admitted frames (ihist_batch_set_io) and uploads them on the copy
+    stream.  plain: one ihist_compute per frame with a plan per shape.
+    Output histograms come from torch's allocator on the compute stream and
+    are returned to it on eviction.
+    """
+
+    def __init__(self, mode="batched", nslots=64, max_shape=(1080, 1920, 64), query_slots=64):
+        import torch
+
+        from . import ihist
+        self.torch, self.ih = torch, ihist
+        self.mode = mode
+        self.stream = torch.cuda.current_stream()
+        self.copy = torch.cuda.Stream()
+        self.s = self.stream.cuda_stream
+        h, w, b = max_shape
+        self.plans = {}
+        self.batches = []
+        self.inputs = []
+        if mode == "batched":
+            for _ in range(2):
+                ins = [torch.empty((h, w), dtype=torch.uint8, device="cuda") for _ in range(nslots)]
+                outs = [torch.empty((b, h, w), dtype=torch.int32, device="cuda") for _ in range(1)] * nslots
+                self.batches.append(ihist.Batch(ins, b, outs=outs))
+                self.inputs.append(ins)
+            del outs
+        else:
+            self.inputs.append([torch.empty((h, w), dtype=torch.uint8, device="cuda") for _ in range(2)])
+        self.next_batch = 0
+        self.next_input = 0
+        self.read_done = [torch.cuda.Event() for _ in range(2)]
+        self.upload_done = [torch.cuda.Event() for _ in range(2)]
+        for e in self.read_done:
+            e.record(self.stream)
+        self.t0_event = torch.cuda.Event(enable_timing=True)
+        self.t0_wall = 0.0
+        self.query_bufs = []
+
+    def start(self):
+        self.torch.cuda.synchronize()
+        self.t0_event.record(self.stream)
+        self.torch.cuda.synchronize()
+        self.t0_wall = time.perf_counter()
+
+    def clock(self):
+        return time.perf_counter() - self.t0_wall
+
+    def _plan(self, h, w, b):
+        p = self.plans.get((h, w, b))
+        if p is None:
+            p = self.plans[(h, w, b)] = self.ih.Plan(h, w, b)
+        return p
+
+    def launch_frames(self, reqs, t):
+        torch, ih = self.torch, self.ih
+        outs = {r.rid: torch.empty((r.nbins, r.h, r.w), dtype=torch.int32, device="cuda") for r in reqs}
+        ev = torch.cuda.Event(enable_timing=True)
+        if self.mode == "batched":
+            b = self.batches[self.next_batch]
+            ins = self.inputs[self.next_batch]
+            self.next_batch ^= 1
+            views = [ins[i].view(-1)[:r.h * r.w].view(r.h, r.w) for i, r in enumerate(reqs)]
+            b.set_io(views, [outs[r.rid] for r in reqs], nbins=[r.nbins for r in reqs],
+                     layouts=[0] * len(reqs), stream=self.s)
+            ih.ihist_batch_upload_compute(b.handle, [r.frame.data_ptr() for r in reqs], self.s,
+                                          self.copy.cuda_stream)
+        else:
+            (r,) = reqs
+            k = self.next_input
+            self.next_input ^= 1
+            view = self.inputs[0][k].view(-1)[:r.h * r.w].view(r.h, r.w)
+            # the upload into buffer k waits only for the compute that last read it
+            self.copy.wait_event(self.read_done[k])
+            with torch.cuda.stream(self.copy):
+                view.copy_(r.frame, non_blocking=True)
+                self.upload_done[k].record(self.copy)
+            self.stream.wait_event(self.upload_done[k])
+            self._plan(r.h, r.w, r.nbins).compute(view, outs[r.rid], stream=self.s)
+            self.read_done[k].record(self.stream)
+        ev.record(self.stream)
+        return {"ev": ev, "payloads": {r.rid: (outs[r.rid], r.h, r.w, r.nbins) for r in reqs}}
+
+    def launch_query(self, q, payload, t):
+        torch = self.torch
+        hist, h, w, b = payload
+        rects = torch.from_numpy(np.ascontiguousarray(q.rects, dtype=np.int32)).pin_memory()
+        d_rects = torch.empty(rects.shape, dtype=torch.int32, device="cuda")
+        d_rects.copy_(rects, non_blocking=True)
+        out = torch.empty((rects.shape[0], b), dtype=torch.int32, device="cuda")
+        self._plan(h, w, b).query(hist, d_rects, out, stream=self.s)
+        host = torch.empty(out.shape, dtype=torch.int32).pin_memory()
+        host.copy_(out, non_blocking=True)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(self.stream)
+        return {"ev": ev, "result": host, "keep": (rects, d_rects, out)}
+
+    def poll(self, handle, t):
+        return handle["ev"].query()
+
+    def done_time(self, handle):
+        return self.t0_event.elapsed_time(handle["ev"]) / 1e3
+
+    def release(self, rid, payload):
+        pass  # dropping the last reference returns the memory to torch's allocator
+
+    def close(self):
+        for b in self.batches:
+            b.close()
+        for p in self.plans.values():
+            p.close()
+
+
+def serve(mode="batched", duration_s=2.0, budget_gb=40.0, seed=None, frame_rate=2000.0, query_rate=200.0,
+          rects_per_query=10000, pool_per_shape=8, saturate=False):
+    """Run the serving workload on the GPU; returns the server's report."""
+    import torch
+    seed = synth.workload_seed(4) if seed is None else seed
+    pool = {}
+    for (w, h) in synth.BATCH_RESOLUTIONS:
+        pool[(h, w)] = [torch.from_numpy(synth.uniform_frame(seed + 100 * k + w, h, w)).pin_memory()
+                        for k in range(pool_per_shape)]
+    reqs = serving_workload(seed, duration_s, frame_rate, query_rate, rects_per_query, pool)
+    if saturate:
+        for r in reqs:
+            r.t_arrival = 0.0
+    ex = GpuExecutor(mode)
+    srv = Server(ex, int(budget_gb * (1 << 30)), mode=mode)
+    ex.start()
+    t0 = time.perf_counter()
+    srv.run(reqs, ex.clock)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    rep = srv.report(wall)
+    rep["wall_s"] = wall
+    rep["requests"] = len(reqs)
+    ex.close()
+    return rep

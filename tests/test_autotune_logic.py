@@ -1,0 +1,51 @@
+"""Autotuner search and cache logic on the CPU (injected timer)."""
+import json
+
+from paper_1711_01919_gb300 import autotune, ihist
+
+
+def test_candidates_respect_warp_limit():
+    for (h, w, b) in [(1080, 1920, 64), (8192, 8192, 128), (240, 320, 16), (5, 3, 2)]:
+        cands = autotune.plan_candidates(h, w, b)
+        assert cands[0] == {}
+        nchunks = -(-w // 128)
+        for t in cands[1:]:
+            wpg = -(-nchunks // t["chunks_per_warp"])
+            assert wpg * t["groups_per_cta"] <= 16 or t["groups_per_cta"] == 1
+            assert wpg <= 16
+            assert t.get("rows_per_band", 0) <= h
+
+
+def test_search_picks_fastest_and_skips_rejected(tmp_path, monkeypatch):
+    monkeypatch.setenv("IHIST_TUNE_CACHE", str(tmp_path / "c.json"))
+    calls = []
+
+    def timer(t):
+        calls.append(t)
+        if t.get("bins_per_cta") == 8:
+            raise ihist.IhistError(ihist.IHIST_ERR_UNSUPPORTED, "plan")
+        return 1.0 / (1 + t.get("rows_per_band", 0)) + 0.01 * t.get("chunks_per_warp", 1)
+
+    best = autotune.tune_plan(1080, 1920, 64, timer=timer, device="fake")
+    assert best["rows_per_band"] == 64 and best["bins_per_cta"] == 4 and best["chunks_per_warp"] == 1
+    cache = json.load(open(tmp_path / "c.json"))
+    assert "plan|fake|1080x1920x64|0" in cache
+    # second call is served from the cache: the timer is not called again
+    n = len(calls)
+    assert autotune.tune_plan(1080, 1920, 64, timer=timer, device="fake") == best
+    assert len(calls) == n
+
+
+def test_batch_tuning_key_and_cache(tmp_path, monkeypatch):
+    monkeypatch.setenv("IHIST_TUNE_CACHE", str(tmp_path / "c.json"))
+    shapes = [(240, 320, 16, 0), (1080, 1920, 64, 0), (240, 320, 16, 0)]
+    best = autotune.tune_batch(shapes, timer=lambda t: abs(t.get("rows_per_band", 0) - 40) + 0.5 * (t.get("bins_per_cta", 4) == 8),
+                               device="fake")
+    assert best == {"bins_per_cta": 4, "rows_per_band": 40}
+    cache = json.load(open(tmp_path / "c.json"))
+    assert any(k.startswith("batch|fake|3|") for k in cache)
+
+
+def test_choose_layout():
+    assert autotune.choose_layout(10, 10, 4, timer=lambda l: 2.0 if l == 0 else 1.0) == ihist.IHIST_PIXEL_MAJOR
+    assert autotune.choose_layout(10, 10, 4, timer=lambda l: 1.0 if l == 0 else 2.0) == ihist.IHIST_BIN_MAJOR

@@ -159,3 +159,46 @@ def test_upload_compute_from_pinned_host_frames():
             torch.cuda.synchronize()
             assert batch.status() == ihist.IHIST_OK
             check_batch(batch, imgs, nb, [0, 0, 0])
+
+
+def test_set_io_rebinds_different_shapes_within_slot_capacity():
+    # plan 4 slots at 480x640x32, then bind smaller and mixed frames
+    cap = [(480, 640, 32)] * 4
+    d0 = [torch.empty((h, w), dtype=torch.uint8, device="cuda") for (h, w, b) in cap]
+    with ihist.Batch(d0, [b for (h, w, b) in cap]) as batch:
+        for shapes in ([(100, 300, 16), (480, 640, 32), (7, 5, 3)],
+                       [(240, 320, 32), (480, 640, 8), (480, 640, 32), (33, 129, 24)],
+                       [(1, 1, 1)]):
+            imgs = [synth.uniform_frame(900 + h + w + b, h, w) for (h, w, b) in shapes]
+            frames = [torch.from_numpy(x).cuda() for x in imgs]
+            outs = [torch.empty((b, h, w), dtype=torch.int32, device="cuda") for (h, w, b) in shapes]
+            batch.nbins = [b for (h, w, b) in shapes]
+            batch.layouts = [0] * len(shapes)
+            batch.set_io(frames, outs)
+            batch.compute()
+            assert batch.status() == ihist.IHIST_OK
+            check_batch(batch, imgs, batch.nbins, batch.layouts)
+        # a frame larger than its slot is refused and the binding stays usable
+        big = torch.empty((960, 640), dtype=torch.uint8, device="cuda")
+        bo = torch.empty((32, 960, 640), dtype=torch.int32, device="cuda")
+        with pytest.raises(ihist.IhistError) as e:
+            ihist.ihist_batch_set_io(batch.handle, [(960, 640, 32, 0, big.data_ptr(), 640, bo.data_ptr())])
+        assert e.value.code == ihist.IHIST_ERR_UNSUPPORTED
+        batch.compute()
+        assert batch.status() == ihist.IHIST_OK
+
+
+def test_set_io_narrower_frames_keep_the_planned_launch_shape():
+    # slots planned at 1920 wide: 1280- and 640-wide frames bound later must
+    # fit the planned chunks per warp and per-CTA carry width
+    d0 = [torch.empty((1080, 1920), dtype=torch.uint8, device="cuda") for _ in range(2)]
+    shapes = [(720, 1280, 32), (480, 640, 16)]
+    imgs = [synth.uniform_frame(40 + h, h, w) for (h, w, b) in shapes]
+    for tune in (None, {"bins_per_cta": 8}):
+        with ihist.Batch(d0, [64, 64], tune=tune) as batch:
+            frames = [torch.from_numpy(x).cuda() for x in imgs]
+            outs = [torch.empty((b, h, w), dtype=torch.int32, device="cuda") for (h, w, b) in shapes]
+            batch.set_io(frames, outs, nbins=[b for (h, w, b) in shapes], layouts=[0, 0])
+            batch.compute()
+            assert batch.status() == ihist.IHIST_OK
+            check_batch(batch, imgs, [b for (h, w, b) in shapes], [0, 0])

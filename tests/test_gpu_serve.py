@@ -1,0 +1,81 @@
+"""Served results equal results computed alone, word for word: each frame's
+resident histogram and each query's rows, in the batched (continuous
+batching) and the plain server, with small pools of distinct frames."""
+import numpy as np
+import pytest
+
+from paper_1711_01919_gb300 import ihist, serve, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1711_01919_gb300 import build as cuda_build
+    cuda_build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def run_server(mode, duration=0.04, budget_gb=40.0, saturate=False):
+    seed = synth.workload_seed(4)
+    pool = {}
+    for (w, h) in synth.BATCH_RESOLUTIONS:
+        pool[(h, w)] = [torch.from_numpy(synth.uniform_frame(seed + 7 * k + w, h, w)).pin_memory() for k in range(3)]
+    reqs = serve.serving_workload(seed, duration, 2000.0, 200.0, 500, pool)
+    if saturate:
+        for r in reqs:
+            r.t_arrival = 0.0
+    ex = serve.GpuExecutor(mode, nslots=16)
+    srv = serve.Server(ex, int(budget_gb * (1 << 30)), max_batch=16, mode=mode)
+    ex.start()
+    srv.run(reqs, ex.clock)
+    torch.cuda.synchronize()
+    return srv, ex, reqs
+
+
+def check_alone(srv, reqs):
+    frames = {r.rid: r for r in reqs if isinstance(r, serve.FrameRequest)}
+    alone = {}
+    plans = {}
+    for rid in srv.store.resident():
+        r = frames[rid]
+        key = (r.h, r.w, r.nbins)
+        if key not in plans:
+            plans[key] = ihist.Plan(*key)
+        ref = plans[key].compute(r.frame.cuda())
+        hist = srv.store.payload(rid)[0]
+        assert torch.equal(hist, ref), "frame %d differs from its histogram computed alone" % rid
+        alone[rid] = ref
+    nq = 0
+    for q in reqs:
+        if isinstance(q, serve.QueryRequest) and q.rid in srv.results and q.target in alone:
+            r = frames[q.target]
+            d_rects = torch.from_numpy(np.ascontiguousarray(q.rects)).cuda()
+            ref = plans[(r.h, r.w, r.nbins)].query(alone[q.target], d_rects)
+            assert torch.equal(srv.results[q.rid], ref.cpu()), "query %d differs" % q.rid
+            nq += 1
+    for p in plans.values():
+        p.close()
+    return nq
+
+
+@pytest.mark.parametrize("mode", ["batched", "plain"])
+def test_served_results_equal_alone(mode):
+    srv, ex, reqs = run_server(mode)
+    done = srv.done
+    assert all(d.status == "ok" for d in done)
+    assert len(done) == len(reqs)
+    nq = check_alone(srv, reqs)
+    assert nq >= 3
+    ex.close()
+
+
+def test_batched_server_under_a_small_budget_evicts_and_stays_exact():
+    srv, ex, reqs = run_server("batched", duration=0.04, budget_gb=1.0, saturate=True)
+    assert srv.store.evicted > 0
+    assert srv.store.used <= 1 << 30
+    assert all(d.status == "ok" for d in srv.done if d.kind == "frame")
+    check_alone(srv, reqs)
+    ex.close()

@@ -1,0 +1,92 @@
+"""Serving loop logic on the CPU (fake executor): admission by HBM footprint,
+LRU eviction of unpinned histograms, continuous batching, query pinning."""
+import numpy as np
+
+from paper_1711_01919_gb300 import serve
+
+
+class Clock:
+    def __init__(self, step=1e-4):
+        self.t, self.step = 0.0, step
+
+    def __call__(self):
+        self.t += self.step
+        return self.t
+
+
+def frames(n, h=10, w=10, b=4, dt=0.0):
+    return [serve.FrameRequest(i, i * dt, h, w, b) for i in range(n)]
+
+
+def test_continuous_batching_groups_arrivals():
+    ex = serve.FakeExecutor(frame_latency=1e-3)
+    srv = serve.Server(ex, budget_bytes=1 << 30)
+    done = srv.run(frames(10), Clock())
+    assert len(done) == 10 and all(d.status == "ok" for d in done)
+    kinds = [l for l in ex.launches if l[0] == "frames"]
+    assert kinds[0][1] == list(range(10))  # all arrived together -> one launch
+
+
+def test_plain_mode_launches_one_frame_each():
+    ex = serve.FakeExecutor()
+    srv = serve.Server(ex, budget_bytes=1 << 30, mode="plain")
+    srv.run(frames(5), Clock())
+    assert [l[1] for l in ex.launches] == [[0], [1], [2], [3], [4]]
+
+
+def test_admission_waits_for_budget_and_evicts_lru():
+    nb = serve.hist_bytes(10, 10, 4)
+    ex = serve.FakeExecutor(frame_latency=1e-3)
+    srv = serve.Server(ex, budget_bytes=3 * nb, max_batch=2)
+    done = srv.run(frames(8, dt=1e-3), Clock(2e-4))
+    assert sum(d.status == "ok" for d in done) == 8
+    assert srv.store.used <= 3 * nb
+    assert srv.store.evicted == 5
+    assert srv.store.resident() == [5, 6, 7]
+
+
+def test_oversized_frame_rejected():
+    ex = serve.FakeExecutor()
+    srv = serve.Server(ex, budget_bytes=100)
+    done = srv.run(frames(2), Clock())
+    assert all(d.status == "rejected" for d in done)
+
+
+def test_query_pins_its_target_until_answered():
+    nb = serve.hist_bytes(10, 10, 4)
+    ex = serve.FakeExecutor(frame_latency=1e-4, query_latency=5e-3)
+    srv = serve.Server(ex, budget_bytes=2 * nb, max_batch=1, seed=0)
+    reqs = frames(1) + [serve.QueryRequest(100, 1e-3, np.zeros((3, 4), np.int32))] + \
+        [serve.FrameRequest(1 + i, 2e-3 + i * 1e-4, 10, 10, 4) for i in range(3)]
+    evicted = []
+    ex.release = lambda rid, payload: evicted.append(rid)
+    done = srv.run(reqs, Clock(1e-4))
+    q = [d for d in done if d.kind == "query"][0]
+    assert q.status == "ok" and q.target == 0
+    # frame 0 is held by the slow query, so the later frames evict each other instead
+    assert evicted == [1, 2]
+    assert 0 in srv.store.resident() and 3 in srv.store.resident()
+
+
+def test_query_without_resident_histogram_is_rejected():
+    ex = serve.FakeExecutor()
+    srv = serve.Server(ex, budget_bytes=1 << 20)
+    done = srv.run([serve.QueryRequest(0, 0.0, np.zeros((1, 4), np.int32))], Clock())
+    assert done[0].status == "rejected"
+
+
+def test_workload_mix():
+    reqs = serve.serving_workload(7, 0.2, rects_per_query=10)
+    nf = sum(isinstance(r, serve.FrameRequest) for r in reqs)
+    nq = len(reqs) - nf
+    assert 320 < nf < 480 and 20 < nq < 60
+    assert all(a.t_arrival <= b.t_arrival for a, b in zip(reqs, reqs[1:]))
+
+
+def test_report_percentiles():
+    ex = serve.FakeExecutor(frame_latency=2e-3)
+    srv = serve.Server(ex, budget_bytes=1 << 30)
+    srv.run(frames(20, dt=1e-4), Clock(1e-4))
+    rep = srv.report(1.0)
+    assert rep["frame"]["completed"] == 20
+    assert rep["frame"]["p50_ms"] <= rep["frame"]["p99_ms"] <= rep["frame"]["max_ms"]
