@@ -18,6 +18,11 @@ integral_histogram_threads(img, nbins, nthreads)  same result, bins split over
                                   threads (timing only; Sec. 4.7 methodology).
 query(hist, rects)                Eq. 2 on an inclusive rect list -> [n][nbins].
 region_brute(img, nbins, rect)    direct count over a rectangle (no Eq. 2).
+bin_of_edges(v, edges)            the bin of v for bins given by edges, or -1.
+integral_histogram_mapped(img, bin_map, nbins)   Algorithm 1 for any value -> bin map.
+integral_histogram_edges(img, edges)             Algorithm 1 for bins given by edges.
+integral_histogram_joint(img, bins)              Algorithm 1 over the joint bins of a
+                                  [h][w][C] frame (channel 0 most significant).
 
 ``Oracle(path)`` wraps any shared object built from ``ihist_oracle.c``; the
 tests use it to load deliberately mutated copies and check that the pins
@@ -99,6 +104,14 @@ class Oracle:
                                             ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, _u32p]
         lib.oracle_region_brute.restype = ctypes.c_int
+        lib.oracle_bin_of_edges.argtypes = [ctypes.c_int, _i32p, ctypes.c_int]
+        lib.oracle_bin_of_edges.restype = ctypes.c_int
+        lib.oracle_ih_mapped.argtypes = [_u8p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _i32p,
+                                         ctypes.c_int, _u32p]
+        lib.oracle_ih_mapped.restype = None
+        lib.oracle_ih_joint.argtypes = [_u8p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        _i32p, _u32p]
+        lib.oracle_ih_joint.restype = None
         self.lib = lib
         self.path = path
 
@@ -159,6 +172,48 @@ class Oracle:
         return out
 
 
+    def bin_of_edges(self, v: int, edges) -> int:
+        """The bin of intensity v for bins given by edges (nbins + 1 ints), or -1."""
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32))
+        return int(self.lib.oracle_bin_of_edges(int(v), e.ctypes.data_as(_i32p), e.size - 1))
+
+    def integral_histogram_mapped(self, img, bin_map, nbins: int, out=None) -> np.ndarray:
+        """Algorithm 1 with bin_map[v] (256 ints in [-1, nbins)) as Q."""
+        a = _img(img)
+        h, w = a.shape
+        m = np.ascontiguousarray(np.asarray(bin_map, dtype=np.int32))
+        if m.shape != (256,) or m.min() < -1 or m.max() >= nbins:
+            raise ValueError("bin_map must be 256 ints in [-1, nbins)")
+        if out is None:
+            out = np.empty((nbins, h, w), dtype=np.uint32)
+        if h and w and nbins:
+            self.lib.oracle_ih_mapped(_p8(a), a.strides[0], h, w, m.ctypes.data_as(_i32p), nbins, _p32(out))
+        return out
+
+    def integral_histogram_edges(self, img, edges, out=None) -> np.ndarray:
+        """Algorithm 1 for bins [edges[k], edges[k+1]); values outside count nowhere."""
+        nbins = len(edges) - 1
+        bin_map = [self.bin_of_edges(v, edges) for v in range(256)]
+        return self.integral_histogram_mapped(img, bin_map, nbins, out)
+
+    def integral_histogram_joint(self, img, bins, out=None) -> np.ndarray:
+        """Algorithm 1 over the joint bins of a uint8 [h][w][C] frame."""
+        a = np.asarray(img)
+        if a.dtype != np.uint8 or a.ndim != 3:
+            raise ValueError("image must be a 3-D uint8 [h][w][C] array")
+        a = np.ascontiguousarray(a)
+        h, w, c = a.shape
+        b = np.ascontiguousarray(np.asarray(bins, dtype=np.int32))
+        if b.shape != (c,):
+            raise ValueError("one bin count per channel")
+        nbins = int(np.prod(b))
+        if out is None:
+            out = np.empty((nbins, h, w), dtype=np.uint32)
+        if h and w:
+            self.lib.oracle_ih_joint(_p8(a), a.strides[0], h, w, c, b.ctypes.data_as(_i32p), _p32(out))
+        return out
+
+
 def default() -> Oracle:
     """The oracle built from ihist_oracle.c as committed."""
     global _default
@@ -190,3 +245,19 @@ def query(hist, rects):
 
 def region_brute(img, nbins, rect):
     return default().region_brute(img, nbins, rect)
+
+
+def bin_of_edges(v, edges):
+    return default().bin_of_edges(v, edges)
+
+
+def integral_histogram_mapped(img, bin_map, nbins, out=None):
+    return default().integral_histogram_mapped(img, bin_map, nbins, out)
+
+
+def integral_histogram_edges(img, edges, out=None):
+    return default().integral_histogram_edges(img, edges, out)
+
+
+def integral_histogram_joint(img, bins, out=None):
+    return default().integral_histogram_joint(img, bins, out)

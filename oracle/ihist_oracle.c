@@ -109,6 +109,77 @@ int oracle_region_brute(const uint8_t *img, size_t pitch, int h, int w,
   return 0;
 }
 
+/* ---- other bin structures and joint (multi-channel) histograms ---------
+ *
+ * Eq. 1 holds for any binning function Q: the paper leaves the bin layout
+ * open (Sec. 2.1) and names other bin structures and higher-dimensional
+ * histograms, such as joint colour histograms, as uses of the same integral
+ * (Sec. 1, Sec. 2.1).  Readings taken here:
+ *   - bins by edges: nbins + 1 strictly increasing integers
+ *     e[0] < e[1] < ... < e[nbins] in [0, 256]; bin k holds the intensities
+ *     v with e[k] <= v < e[k+1]; intensities outside [e[0], e[nbins]) are in
+ *     no bin (they count nowhere).
+ *   - any value -> bin map: map[v] in [-1, nbins), -1 meaning no bin.
+ *   - joint bins of a pixel with C interleaved channels (p_0 .. p_{C-1}),
+ *     channel c cut into bins[c] uniform bins as above: the joint bin is the
+ *     mixed-radix number of the channel bins, channel 0 most significant,
+ *       k = (...((q_0 * bins[1] + q_1) * bins[2] + q_2) ...)
+ *     with q_c = Q(p_c) among bins[c] bins; nbins = prod bins[c].
+ * Every plane is still built by Algorithm 1's recurrence. */
+
+/* The bin of intensity v for bins given by edges, or -1. */
+int oracle_bin_of_edges(int v, const int *edges, int nbins) {
+  for (int k = 0; k < nbins; ++k)
+    if (edges[k] <= v && v < edges[k + 1]) return k;
+  return -1;
+}
+
+/* Algorithm 1 with Q(k, v) = [map[v] == k]; out is [nbins][h][w] uint32. */
+void oracle_ih_mapped(const uint8_t *img, size_t pitch, int h, int w,
+                      const int *map, int nbins, uint32_t *out) {
+  for (int k = 0; k < nbins; ++k) {
+    uint32_t *plane = out + (size_t)k * h * w;
+    for (int x = 0; x < h; ++x) {
+      for (int y = 0; y < w; ++y) {
+        uint32_t above = (x > 0) ? plane[(size_t)(x - 1) * w + y] : 0u;
+        uint32_t left = (y > 0) ? plane[(size_t)x * w + (y - 1)] : 0u;
+        uint32_t diag = (x > 0 && y > 0) ? plane[(size_t)(x - 1) * w + (y - 1)] : 0u;
+        uint32_t q = (map[img[(size_t)x * pitch + y]] == k) ? 1u : 0u;
+        plane[(size_t)x * w + y] = above + left - diag + q;
+      }
+    }
+  }
+}
+
+/* Joint bin of one pixel px[0 .. channels-1]. */
+int oracle_joint_bin(const uint8_t *px, int channels, const int *bins) {
+  int k = 0;
+  for (int c = 0; c < channels; ++c) k = k * bins[c] + oracle_bin_of(px[c], bins[c]);
+  return k;
+}
+
+/* Algorithm 1 over the joint bins of a pixel-interleaved C-channel frame:
+ * img holds h rows of w * channels bytes at row stride pitch; out is
+ * [prod bins][h][w] uint32. */
+void oracle_ih_joint(const uint8_t *img, size_t pitch, int h, int w,
+                     int channels, const int *bins, uint32_t *out) {
+  int nbins = 1;
+  for (int c = 0; c < channels; ++c) nbins *= bins[c];
+  for (int k = 0; k < nbins; ++k) {
+    uint32_t *plane = out + (size_t)k * h * w;
+    for (int x = 0; x < h; ++x) {
+      for (int y = 0; y < w; ++y) {
+        uint32_t above = (x > 0) ? plane[(size_t)(x - 1) * w + y] : 0u;
+        uint32_t left = (y > 0) ? plane[(size_t)x * w + (y - 1)] : 0u;
+        uint32_t diag = (x > 0 && y > 0) ? plane[(size_t)(x - 1) * w + (y - 1)] : 0u;
+        const uint8_t *px = img + (size_t)x * pitch + (size_t)y * channels;
+        uint32_t q = (oracle_joint_bin(px, channels, bins) == k) ? 1u : 0u;
+        plane[(size_t)x * w + y] = above + left - diag + q;
+      }
+    }
+  }
+}
+
 /* ---- bins-parallel variant, for timing the CPU on all host cores ------ */
 
 typedef struct {

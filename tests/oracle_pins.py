@@ -13,6 +13,12 @@ value.  Expected values come from:
   * closed forms: constant frame, column ramp, row ramp, single bright pixel;
   * special cases of the binning: power-of-two B is a right shift, every
     bin is a contiguous run of width floor(256/B) or ceil(256/B).
+
+Other bin structures (edges, any value -> bin map) and joint multi-channel
+bins are pinned the same way: hand-worked fixtures, numpy's binary search
+(``searchsorted``) as an independent bin lookup, brute-force counting,
+reduction to the pinned uniform case, and marginals of the joint histogram
+that must equal the single-channel integral histograms.
 """
 from __future__ import annotations
 
@@ -56,6 +62,27 @@ def brute_integral_histogram(img: np.ndarray, nbins: int) -> np.ndarray:
     return out
 
 
+def brute_from_bins(bins: np.ndarray, nbins: int) -> np.ndarray:
+    """Eq. 1 as a literal count, given each pixel's bin (-1 = no bin)."""
+    h, w = bins.shape
+    out = np.zeros((nbins, h, w), dtype=np.uint32)
+    for y in range(h):
+        for x in range(w):
+            counts = [0] * nbins
+            for r in range(y + 1):
+                for c in range(x + 1):
+                    if bins[r, c] >= 0:
+                        counts[bins[r, c]] += 1
+            out[:, y, x] = counts
+    return out
+
+
+def edges_bin(v: int, edges) -> int:
+    """Bin of v for bins [e_k, e_k+1), by numpy's binary search; -1 outside."""
+    k = int(np.searchsorted(np.asarray(edges), v, side="right")) - 1
+    return k if 0 <= k < len(edges) - 1 else -1
+
+
 def brute_region(img: np.ndarray, nbins: int, rect) -> np.ndarray:
     x0, y0, x1, y1 = rect
     out = np.zeros(nbins, dtype=np.uint32)
@@ -80,10 +107,14 @@ def load_golden(name: str) -> dict:
     while i < len(lines):
         tok = lines[i].split()
         i += 1
-        if tok[0] in ("h", "w", "bins"):
+        if tok[0] in ("h", "w", "bins", "channels"):
             d[tok[0]] = int(tok[1])
+        elif tok[0] in ("edges", "cbins"):
+            d[tok[0]] = [int(v) for v in tok[1:]]
         elif tok[0] == "image":
             d["image"] = rows(d["h"]).astype(np.uint8)
+            if "channels" in d:
+                d["image"] = d["image"].reshape(d["h"], d["w"], d["channels"])
         elif tok[0] == "H":
             d["planes"][int(tok[1])] = rows(d["h"])
         elif tok[0] == "rest":
@@ -105,6 +136,8 @@ def load_golden(name: str) -> dict:
 
 
 GOLDEN_FILES = ("ih_3x4_b2.txt", "ih_2x4_b3_edges.txt", "ih_2x2_b256.txt")
+GOLDEN_EDGES = "ih_2x4_b3_edges_gap.txt"
+GOLDEN_JOINT = "ih_2x2_joint_2x3x2.txt"
 TINY_BINS = (1, 2, 3, 5, 8, 32, 256)
 
 
@@ -264,5 +297,106 @@ def check_threads(o) -> None:
         assert np.array_equal(got, ref), t
 
 
+def check_fixture(d, H, name) -> None:
+    H = H.astype(np.int64)
+    for b, plane in d["planes"].items():
+        assert np.array_equal(H[b], plane), (name, b)
+    if d["rest_zero"]:
+        others = [b for b in range(d["bins"]) if b not in d["planes"]]
+        assert not H[others].any(), name
+    else:
+        assert sorted(d["planes"]) == list(range(d["bins"])), name
+
+
+EDGE_SETS = ([0, 256], [10, 50, 51, 200], [0, 1, 2, 255, 256], [100, 101], [0, 64, 65, 128, 250],
+             [3, 17, 90, 91, 92, 200, 255])
+
+
+def check_edges(o) -> None:
+    """Bins given by edges: fixture, numpy lookup, uniform reduction, brute force."""
+    d = load_golden(GOLDEN_EDGES)
+    H = o.integral_histogram_edges(d["image"], d["edges"])
+    check_fixture(d, H, GOLDEN_EDGES)
+    for rect, exp in d["queries"]:
+        assert np.array_equal(o.query(H, [rect])[0].astype(np.int64), exp), rect
+    for edges in EDGE_SETS:
+        for v in range(256):
+            assert o.bin_of_edges(v, edges) == edges_bin(v, edges), (edges, v)
+    # uniform edges e_k = ceil(256 k / B) give the uniform bins of Eq. 1's Q
+    rng = np.random.default_rng(31)
+    img = rng.integers(0, 256, size=(9, 14), dtype=np.uint8)
+    for nbins in (1, 3, 7, 64, 256):
+        edges = [-(-256 * k // nbins) for k in range(nbins + 1)]
+        assert np.array_equal(o.integral_histogram_edges(img, edges), o.integral_histogram(img, nbins)), nbins
+    for img in tiny_images()[:6]:
+        for edges in EDGE_SETS[1:4]:
+            bins = np.vectorize(lambda v: edges_bin(int(v), edges))(img)
+            exp = brute_from_bins(bins, len(edges) - 1)
+            assert np.array_equal(o.integral_histogram_edges(img, edges), exp), (img.shape, edges)
+
+
+def check_mapped(o) -> None:
+    """Any value -> bin map: brute force, plane permutation, values in no bin."""
+    rng = np.random.default_rng(77)
+    img = rng.integers(0, 256, size=(11, 19), dtype=np.uint8)
+    nbins = 6
+    bin_map = rng.integers(-1, nbins, size=256)
+    H = o.integral_histogram_mapped(img, bin_map, nbins)
+    assert np.array_equal(H, brute_from_bins(bin_map[img], nbins))
+    # renaming the bins renames the planes
+    perm = rng.permutation(nbins)
+    renamed = np.where(bin_map >= 0, perm[np.maximum(bin_map, 0)], -1)
+    H2 = o.integral_histogram_mapped(img, renamed, nbins)
+    for k in range(nbins):
+        assert np.array_equal(H2[perm[k]], H[k]), k
+    # the sum over bins counts exactly the pixels that have a bin
+    inbin = (bin_map[img] >= 0).astype(np.int64)
+    assert np.array_equal(H.astype(np.int64).sum(axis=0), inbin.cumsum(axis=0).cumsum(axis=1))
+    assert not o.integral_histogram_mapped(img, np.full(256, -1), 3).any()
+
+
+def joint_digits(k: int, cbins) -> list:
+    """Channel bins of joint bin k (channel 0 most significant)."""
+    out = []
+    for b in reversed(cbins):
+        out.append(k % b)
+        k //= b
+    return out[::-1]
+
+
+def check_joint(o) -> None:
+    """Joint multi-channel bins: fixture, one channel, marginals, brute force."""
+    d = load_golden(GOLDEN_JOINT)
+    H = o.integral_histogram_joint(d["image"], d["cbins"])
+    assert H.shape[0] == d["bins"]
+    check_fixture(d, H, GOLDEN_JOINT)
+    for rect, exp in d["queries"]:
+        assert np.array_equal(o.query(H, [rect])[0].astype(np.int64), exp), rect
+    rng = np.random.default_rng(5)
+    img1 = rng.integers(0, 256, size=(8, 13, 1), dtype=np.uint8)
+    for b in (1, 5, 16):
+        assert np.array_equal(o.integral_histogram_joint(img1, [b]), o.integral_histogram(img1[:, :, 0], b)), b
+    # summing the joint planes over the other channels' bins leaves channel
+    # c's own integral histogram (pins the digit order and each channel's Q)
+    for cbins in ([2, 3, 4], [5, 2], [4, 1, 3, 2]):
+        C = len(cbins)
+        img = rng.integers(0, 256, size=(7, 10, C), dtype=np.uint8)
+        H = o.integral_histogram_joint(img, cbins).astype(np.int64)
+        assert H.shape[0] == int(np.prod(cbins))
+        digits = np.array([joint_digits(k, cbins) for k in range(H.shape[0])])
+        for c in range(C):
+            ref = o.integral_histogram(np.ascontiguousarray(img[:, :, c]), cbins[c]).astype(np.int64)
+            for j in range(cbins[c]):
+                assert np.array_equal(H[digits[:, c] == j].sum(axis=0), ref[j]), (cbins, c, j)
+    img = rng.integers(0, 256, size=(5, 6, 3), dtype=np.uint8)
+    cbins = [3, 2, 4]
+    bins = np.zeros((5, 6), dtype=np.int64)
+    for y in range(5):
+        for x in range(6):
+            q = [brute_bin(int(img[y, x, c]), cbins[c]) for c in range(3)]
+            bins[y, x] = (q[0] * cbins[1] + q[1]) * cbins[2] + q[2]
+    assert np.array_equal(o.integral_histogram_joint(img, cbins), brute_from_bins(bins, 24))
+
+
 ALL_CHECKS = (check_bins, check_golden, check_brute_force, check_invariants,
-              check_closed_forms, check_query, check_threads)
+              check_closed_forms, check_query, check_threads, check_edges, check_mapped, check_joint)

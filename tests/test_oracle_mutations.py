@@ -24,6 +24,17 @@ MUTATIONS = [
     ("brute_region_open_end", "for (int r = y0; r <= y1; ++r)", "for (int r = y0; r < y1; ++r)"),
     ("threads_skip_last_bin", "for (int k = j->first; k < j->nbins; k += j->stride)",
      "for (int k = j->first; k < j->nbins - 1; k += j->stride)"),
+    ("edges_closed_upper", "if (edges[k] <= v && v < edges[k + 1]) return k;",
+     "if (edges[k] <= v && v <= edges[k + 1]) return k;"),
+    ("edges_outside_to_last_bin", "  return -1;\n}\n\n/* Algorithm 1 with Q(k, v)",
+     "  return nbins - 1;\n}\n\n/* Algorithm 1 with Q(k, v)"),
+    ("mapped_no_bin_counts_in_bin_0", "uint32_t q = (map[img[(size_t)x * pitch + y]] == k) ? 1u : 0u;",
+     "uint32_t q = (map[img[(size_t)x * pitch + y]] == k || (k == 0 && map[img[(size_t)x * pitch + y]] < 0)) ? 1u : 0u;"),
+    ("joint_channel_order", "k = k * bins[c] + oracle_bin_of(px[c], bins[c]);",
+     "k = k * bins[c] + oracle_bin_of(px[channels - 1 - c], bins[c]);"),
+    ("joint_radix", "k = k * bins[c] + oracle_bin_of(px[c], bins[c]);",
+     "k = k + oracle_bin_of(px[c], bins[c]) * (c ? bins[c - 1] : 1);"),
+    ("joint_pixel_stride", "img + (size_t)x * pitch + (size_t)y * channels;", "img + (size_t)x * pitch + (size_t)y;"),
 ]
 
 
