@@ -51,6 +51,11 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=0, help="0 = min(steps, 30)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (640x480, uneven 256-frame batch, 8192x8192) "
+                         "and the other bin structures (edges, joint RGB)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="simulated seconds of the serving workload per server mode (0 = skip)")
     ap.add_argument("--frames", type=int, default=64,
                     help="frames per step (64 = the workload; smaller only for profiler captures)")
     return ap.parse_args()
@@ -222,6 +227,170 @@ def run_reference(args):
     return 0
 
 
+def serving_report(seconds: float) -> dict:
+    """Served p50/p99 per request class, continuous batching against plain
+    per-frame launches, on the same Poisson request stream (frames of the
+    uneven mix at 2000/s, queries of 10,000 rectangles at 200/s), and the
+    frame throughput of both servers when the same requests arrive 1000x
+    faster than they can be served."""
+    from paper_1711_01919_gb300 import serve
+
+    keep = ("completed", "rejected", "p50_ms", "p99_ms", "per_s")
+    out = {"workload": "Poisson arrivals for %.1f s: frames at 2000/s (320x240..1920x1080, 16-64 bins), "
+                       "queries of 10,000 rects at 200/s against a random resident histogram; "
+                       "40 GB budget, LRU eviction" % seconds}
+    for mode in ("batched", "plain"):
+        rep = serve.serve(mode=mode, duration_s=seconds)
+        out[mode] = {k: {f: rep[k][f] for f in keep} for k in ("frame", "query")}
+        out[mode]["evicted"] = rep["evicted"]
+    for mode in ("batched", "plain"):
+        rep = serve.serve(mode=mode, duration_s=seconds / 4, saturate=True)
+        out["saturated_" + mode] = {"frames_per_s": rep["frame"]["per_s"], "frames": rep["frame"]["completed"],
+                                    "frame_p99_ms": rep["frame"]["p99_ms"]}
+    return out
+
+
+def _median_ms(fn, stream, reps: int = 5, warm: int = 3) -> float:
+    import torch
+    for _ in range(warm):
+        fn()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def configs_report(stream, peak: float) -> dict:
+    """The other workloads of the method, each timed on its own (median of 5
+    after 3 warm-ups, CUDA events): one 640x480 frame with 32 bins and 1000
+    queries per launch pair (8 frames and 8 outputs in rotation, 315 MB > L2);
+    a 256-frame batch of uneven size (320x240 .. 1920x1080, 16/32/64 bins) in
+    one persistent launch, default and autotuned tiling, the autotuned one
+    also replayed from a captured CUDA graph; one 8192x8192 frame with 128
+    bins (34.4 GB out) and 2^20 queries on it."""
+    import torch
+
+    from paper_1711_01919_gb300 import autotune, ihist, synth
+    s = stream.cuda_stream
+    rep = {}
+    # 640x480, 32 bins, 1000 queries
+    h, w, b = 480, 640, 32
+    seed = synth.workload_seed(1)
+    fr = [torch.from_numpy(synth.uniform_frame(synth.substream_seed(seed, i), h, w)).cuda() for i in range(8)]
+    ou = [torch.empty((b, h, w), dtype=torch.int32, device="cuda") for _ in range(8)]
+    rects = torch.from_numpy(synth.rects(seed + 1, 1000, h, w)).cuda()
+    q = torch.empty((1000, b), dtype=torch.int32, device="cuda")
+    with ihist.Plan(h, w, b) as plan:
+        def vga():
+            for i in range(64):
+                ihist.ihist_compute(plan.handle, fr[i % 8].data_ptr(), w, ou[i % 8].data_ptr(), s)
+                ihist.ihist_query(plan.handle, ou[i % 8].data_ptr(), rects.data_ptr(), 1000, q.data_ptr(), s)
+        ms = _median_ms(vga, stream)
+        if plan.status() != ihist.IHIST_OK:
+            raise SystemExit("device status error in the 640x480 run")
+        byts = 64 * (h * w * b * 4 + h * w)
+        rep["vga_640x480_b32_1000q"] = {"frames_per_s": 64e3 / ms, "us_per_frame": ms * 1e3 / 64,
+                                        "gbs": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak,
+                                        "form": "ihist_compute + ihist_query per frame"}
+    del fr, ou, rects, q
+    # 256 uneven frames in one launch
+    specs = synth.uneven_batch_specs(synth.workload_seed(3), 256)
+    fr = [torch.from_numpy(synth.uniform_frame(sd, h, w)).cuda() for (h, w, nb, sd) in specs]
+    ou = [torch.empty((nb, h, w), dtype=torch.int32, device="cuda") for (h, w, nb, sd) in specs]
+    nbs = [nb for (h, w, nb, sd) in specs]
+    byts = sum(h * w * nb * 4 + h * w for (h, w, nb, sd) in specs)
+    entry = {"frames": 256, "algorithmic_bytes": byts, "form": "one ihist_batch_compute launch"}
+    for label, tune in (("default", None), ("autotuned", "auto")):
+        with ihist.Batch(fr, nbs, outs=ou, tune=tune) as batch:
+            ms = _median_ms(batch.compute, stream)
+            if batch.status() != ihist.IHIST_OK:
+                raise SystemExit("device status error in the uneven batch")
+            entry[label] = {"ms": ms, "frames_per_s": 256e3 / ms, "gbs": byts / ms / 1e6,
+                            "frac": byts / ms / 1e6 / peak, "items": batch.items()}
+            if tune == "auto":
+                entry[label]["tune"] = autotune.tune_batch([(h, w, nb, 0) for (h, w, nb, sd) in specs])
+                # the same launch captured once in a CUDA graph and replayed
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    batch.compute()
+                gms = _median_ms(g.replay, stream)
+                if batch.status() != ihist.IHIST_OK:
+                    raise SystemExit("device status error in the graph replay")
+                entry[label]["graph_replay_ms"] = gms
+                entry[label]["graph_replay_frac"] = byts / gms / 1e6 / peak
+    rep["uneven_256_batch"] = entry
+    del fr, ou
+    torch.cuda.empty_cache()
+    # 8192 x 8192, 128 bins, 2^20 queries
+    h = w = 8192
+    b = 128
+    img = torch.from_numpy(synth.sinusoid_frame(synth.workload_seed(5), h, w)).cuda()
+    out = torch.empty((b, h, w), dtype=torch.int32, device="cuda")
+    rects = torch.from_numpy(synth.rects(synth.workload_seed(5) + 1, 1 << 20, h, w)).cuda()
+    q = torch.empty((1 << 20, b), dtype=torch.int32, device="cuda")
+    with ihist.Plan(h, w, b) as plan:
+        ms = _median_ms(lambda: ihist.ihist_compute(plan.handle, img.data_ptr(), w, out.data_ptr(), s), stream,
+                        reps=3, warm=2)
+        qms = _median_ms(lambda: ihist.ihist_query(plan.handle, out.data_ptr(), rects.data_ptr(), 1 << 20,
+                                                   q.data_ptr(), s), stream, reps=3, warm=2)
+        if plan.status() != ihist.IHIST_OK:
+            raise SystemExit("device status error in the 8192x8192 run")
+        byts = h * w * b * 4 + h * w
+        rep["mp64_8192x8192_b128"] = {"scan_ms": ms, "gbs": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak,
+                                      "query_ms_2p20_rects": qms, "tile": plan.tune}
+    del img, out, rects, q
+    torch.cuda.empty_cache()
+    return rep
+
+
+def other_bins_report(d_frames, outs, stream, steps: int = 5) -> dict:
+    """Per-frame launches with other bin structures on the same 1080p
+    frames and output buffers: 64 non-uniform bins given by edges, and the
+    joint 4 x 4 x 4 bins of three-channel frames.  Algorithmic bytes are the
+    output words plus one read of the frame (three bytes per pixel for the
+    joint case)."""
+    import torch
+
+    from paper_1711_01919_gb300 import ihist
+    n = d_frames.shape[0]
+    s = stream.cuda_stream
+    edges = [3 * k + (k * k) // 64 for k in range(NBINS + 1)]  # widths 3..5, non-uniform
+    rgb = torch.stack([d_frames, d_frames.roll(1, 0), d_frames.roll(2, 0)], dim=3).contiguous()
+    out = {}
+    for name, plan, inp, pitch, read_bytes in (
+            ("edges_64_nonuniform", ihist.Plan(H, W, edges=edges), d_frames, W, H * W),
+            ("joint_rgb_4x4x4", ihist.Plan(H, W, bins_per_channel=[4, 4, 4]), rgb, 3 * W, 3 * H * W)):
+
+        def loop():
+            for f in range(n):
+                ihist.ihist_compute(plan.handle, inp[f].data_ptr(), pitch, outs[f].data_ptr(), s)
+
+        for _ in range(3):
+            loop()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            loop()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if plan.status() != ihist.IHIST_OK:
+            raise SystemExit("device status error in the %s run" % name)
+        sec = a.elapsed_time(b) / 1000.0
+        byts = steps * n * (H * W * NBINS * 4 + read_bytes)
+        out[name] = {"frames_per_s": steps * n / sec, "gbs": byts / sec / 1e9,
+                     "form": "%d x ihist_compute per step" % n, "tile": plan.tune}
+        plan.close()
+    del rgb
+    return out
+
+
 def main():
     global NFRAMES
     args = parse_args()
@@ -371,6 +540,22 @@ def main():
     if not torch.equal(h_query.view(NFRAMES, NRECTS, NBINS)[NFRAMES - 1], resident_query):
         raise SystemExit("e2e query results differ from the device-resident run")
 
+    other_bins = None if args.no_configs else other_bins_report(d_frames, outs, stream)
+
+    # ---- write-only probe: the store bandwidth a plain fill reaches on this GPU ----
+    probe = torch.empty((1 << 30,), dtype=torch.int32, device=dev)
+    for _ in range(3):
+        probe.fill_(1)
+    w_start, w_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    w_start.record(stream)
+    for _ in range(10):
+        probe.fill_(1)
+    w_end.record(stream)
+    torch.cuda.synchronize()
+    write_probe_gbs = 10 * probe.numel() * 4 / (w_start.elapsed_time(w_end) / 1000.0) / 1e9
+    del probe
+
     times = torch.tensor([elapsed_ms, e2e_ms, plain_ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(times, op=dist.ReduceOp.MAX)
@@ -405,7 +590,9 @@ def main():
                          "frac": achieved / peak, "traffic": profiled_traffic(),
                          "kernel": "ihist::batch_kernel (%d frames per launch)" % NFRAMES,
                          "bytes_per_launch": bytes_per_launch,
-                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind},
+                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
+                         "write_probe_gbs": write_probe_gbs,
+                         "frac_of_write_probe": achieved / write_probe_gbs},
             "e2e": {"value": world * NFRAMES * e2e_steps / (e2e_ms / 1000.0), "unit": "frames/s",
                     "h2d_bytes_per_step": NFRAMES * H * W, "d2h_bytes_per_step": NFRAMES * NRECTS * NBINS * 4,
                     "steps": e2e_steps,
@@ -415,6 +602,13 @@ def main():
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
         }
+        if not args.no_configs:
+            for v in other_bins.values():
+                v["frac"] = v["gbs"] / peak
+            line["other_bins"] = other_bins
+            line["other_workloads"] = configs_report(stream, peak)
+        if args.serve_seconds > 0:
+            line["serving"] = serving_report(args.serve_seconds)
         if not args.no_cpu_baseline:
             import oracle
             oracle.build()

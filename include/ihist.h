@@ -74,7 +74,12 @@ typedef struct ihist_plan_s *ihist_plan_t;
  *                   IHIST_ERR_LOOKBACK_TIMEOUT (default 2,000,000 us)
  *   fault_skip_band test hook, -1 = off: the CTAs of this band publish no
  *                   carries, so the band below must time out.  Used only
- *                   to test failure detection; never set it otherwise.   */
+ *                   to test failure detection; never set it otherwise.
+ *   warps_per_cta   batched launches: warps per CTA (4, 8 or 16; default
+ *                   8 when every frame is at most 4096 columns wide, else
+ *                   16).  A frame needs ceil(w/128) <= 4 x warps_per_cta.
+ *                   Plans derive it from the tiling, ignore it on input
+ *                   and report it in ihist_plan_get_tune.                 */
 typedef struct {
   int rows_per_band;
   int bins_per_cta;
@@ -83,7 +88,8 @@ typedef struct {
   unsigned int timeout_us;
   int fault_skip_band;
   int groups_per_cta;
-  int reserved[3];
+  int warps_per_cta;
+  int reserved[2];
 } ihist_tune_t;
 
 /* Create a plan for frames of h rows x w columns and nbins bins in the given
@@ -96,6 +102,48 @@ int ihist_plan(int h, int w, int nbins, int layout, ihist_plan_t *out);
 int ihist_plan_tuned(int h, int w, int nbins, int layout, const ihist_tune_t *tune,
                      ihist_plan_t *out);
 
+/* Other bin structures (Sec. 1 / Sec. 2.1: the paper leaves the binning Q
+ * of Eq. 1 open).  Same limits, tiling, workspace and error rules as
+ * ihist_plan_tuned (tune may be NULL); bins_per_cta must be 4 or 8.
+ *   ihist_plan_lut    any value -> bin map: bin_of_value is a HOST array of
+ *                     256 ints, bin_of_value[v] in [0, nbins) is the bin of
+ *                     intensity v and -1 puts v in no bin (such pixels count
+ *                     nowhere).  The table is copied into the plan.
+ *   ihist_plan_edges  bins by edges: edges is a HOST array of nbins + 1
+ *                     strictly increasing ints in [0, 256]; bin k holds the
+ *                     intensities edges[k] <= v < edges[k+1] and values
+ *                     outside [edges[0], edges[nbins]) are in no bin.
+ * The map is applied inside the scan kernel from a 256-entry table in
+ * shared memory; ihist_compute, ihist_query and ihist_sequence_host work on
+ * these plans unchanged.  IHIST_ERR_INVALID_ARG for an entry out of range or
+ * edges that do not increase. */
+int ihist_plan_lut(int h, int w, int nbins, int layout, const int *bin_of_value,
+                   const ihist_tune_t *tune, ihist_plan_t *out);
+int ihist_plan_edges(int h, int w, int nbins, int layout, const int *edges,
+                     const ihist_tune_t *tune, ihist_plan_t *out);
+
+/* Joint histogram of a multi-channel frame (the higher-dimensional, e.g.
+ * colour, histograms of Sec. 1 / Sec. 2.1).  Frames hold `channels` (1..4)
+ * interleaved bytes per pixel: pixel (y, x) channel c at
+ * d_in[y * in_pitch + x * channels + c], in_pitch >= w * channels.  Channel
+ * c is cut into bins_per_channel[c] uniform bins, q_c = floor(v_c * B_c /
+ * 256), and the pixel's bin is the mixed-radix number
+ * k = (...(q_0 * B_1 + q_1) * B_2 + ...) + q_{C-1}   (channel 0 most
+ * significant), so the plan has nbins = prod B_c planes, at most 256
+ * (IHIST_ERR_UNSUPPORTED above that or when w * channels > 65535).
+ * bins_per_channel is a HOST array of `channels` ints in 1..256.  Each
+ * ihist_compute first writes the pixels' joint bins into a plane the plan
+ * owns (h x w bytes, one extra read of the frame), then runs the scan on it;
+ * the output is H[k][y][x] (or pixel-major) exactly as for nbins uniform
+ * bins.  ihist_query and ihist_sequence_host (frames of h * w * channels
+ * bytes) work unchanged. */
+int ihist_plan_joint(int h, int w, int channels, const int *bins_per_channel, int layout,
+                     const ihist_tune_t *tune, ihist_plan_t *out);
+
+/* Bytes per pixel of the plan's input frames: the channel count of a joint
+ * plan, 1 otherwise (0 for a NULL plan). */
+int ihist_plan_channels(ihist_plan_t plan);
+
 /* The tiling a plan resolved to (all fields filled). */
 int ihist_plan_get_tune(ihist_plan_t plan, ihist_tune_t *out);
 
@@ -106,8 +154,8 @@ size_t ihist_workspace_bytes(ihist_plan_t plan);
 size_t ihist_output_bytes(int h, int w, int nbins);
 
 /* Integral histogram of one frame (Eq. 1; fused quantise, row scan, column
- * scan and carry passing).  d_in: h rows of w bytes, row stride in_pitch
- * (>= w) bytes.  d_out: ihist_output_bytes(h, w, nbins) bytes in the plan's
+ * scan and carry passing).  d_in: h rows of w bytes (w * channels for a
+ * joint plan), row stride in_pitch (>= that) bytes.  d_out: ihist_output_bytes(h, w, nbins) bytes in the plan's
  * layout; every word is written exactly once.  The fast path wants d_in and
  * in_pitch 4-byte aligned and d_out 16-byte aligned with w % 4 == 0;
  * anything else takes a slower element-wise path with the same result. */
@@ -166,9 +214,11 @@ typedef struct {
 
 /* Plan a batch of n >= 1 frames (limits per frame as for ihist_plan); the
  * frames also fix the capacity of the batch's n slots (see
- * ihist_batch_set_io).  tune may be NULL; its bins_per_cta (4 or 8) and
- * rows_per_band apply to every frame; chunks per warp and groups per CTA
- * are chosen per frame to fill a CTA of up to 16 warps.  Frames bound
+ * ihist_batch_set_io).  tune may be NULL; its bins_per_cta (4 or 8),
+ * rows_per_band and warps_per_cta apply to every frame; chunks per warp and
+ * groups per CTA are chosen per frame to fill the CTA's warps.  Frames wider
+ * than 4 x warps_per_cta chunks of 128 columns give IHIST_ERR_UNSUPPORTED
+ * (at most 8192 columns with 16 warps).  Frames bound
  * later by ihist_batch_set_io keep within the launch shape the planned
  * frames fixed (chunks per warp, carry width per CTA), which may leave some
  * of a narrower frame's CTA idle.  Allocates the batch's device workspace

@@ -2,7 +2,8 @@
 measurement, cached per device and frame shape.
 
 Search space (ihist_tune_t fields): rows per band R, bins per CTA G (4 or
-8), 128-column chunks per warp m, bin groups per CTA.  Each candidate is
+8), 128-column chunks per warp m, bin groups per CTA (and, for batches,
+warps per CTA).  Each candidate is
 timed with CUDA events on a seeded uniform frame (median of a few launches
 after warm-up); candidates the library rejects (shared memory, registers)
 are skipped.  For a batch the search covers R and G of the batched launch.
@@ -53,8 +54,8 @@ def plan_candidates(h: int, w: int, nbins: int):
     for G in (4, 8):
         for m in (1, 2, 4, 8):
             wpg = -(-nchunks // m)
-            if wpg > 16 or (m > 1 and -(-nchunks // (m // 2)) <= 16 and nchunks <= 16):
-                continue  # needs more than 16 warps, or a smaller m already fits
+            if wpg > 16 or (m > 1 and wpg < 2):
+                continue  # needs more than 16 warps, or leaves a single warp per group
             ngroups = -(-nbins // G)
             for gpc in sorted({1, min(ngroups, max(1, 16 // wpg))}):
                 for R in (0, 16, 24, 32, 48, 64):
@@ -68,7 +69,8 @@ def plan_candidates(h: int, w: int, nbins: int):
 
 
 def batch_candidates():
-    return [{}] + [{"bins_per_cta": G, "rows_per_band": R} for G in (4, 8) for R in (16, 24, 32, 40, 48, 64)]
+    return [{}] + [{"warps_per_cta": nw, "bins_per_cta": G, "rows_per_band": R}
+                   for nw in (8, 16) for G in (4, 8) for R in (24, 32, 40, 48, 56)]
 
 
 def _device_key():
@@ -152,7 +154,7 @@ def tune_plan(h, w, nbins, layout=ihist.IHIST_BIN_MAJOR, timer=None, device=None
 
 
 def tune_batch(shapes, timer=None, device=None, use_cache=True):
-    """Best (bins_per_cta, rows_per_band) for a batch of (h, w, nbins, layout) frames."""
+    """Best (warps_per_cta, bins_per_cta, rows_per_band) for a batch of (h, w, nbins, layout) frames."""
     device = device or _device_key()
     sig = ",".join("%dx%dx%dx%d" % tuple(s) for s in sorted(set(tuple(s) for s in shapes)))
     key = "batch|%s|%d|%s" % (device, len(shapes), sig)

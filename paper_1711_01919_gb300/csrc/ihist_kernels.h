@@ -18,10 +18,13 @@ using BatchFn = void (*)(const FrameDesc *, const CUtensorMap *, const unsigned 
 ScanFn scan_fn_g4(int mmax, bool tma, bool vec);
 ScanFn scan_fn_g8(int mmax, bool tma, bool vec);
 ScanFn scan_fn_g16(int mmax, bool tma, bool vec);
+ScanFn scan_fn_lut_g4(int mmax, bool tma, bool vec);  // binning through a value -> bin table
+ScanFn scan_fn_lut_g8(int mmax, bool tma, bool vec);
 BatchFn batch_fn_g4(int mmax, bool tma, bool vec);
 BatchFn batch_fn_g8(int mmax, bool tma, bool vec);
 
-inline ScanFn scan_fn(int G, int mmax, bool tma, bool vec) {
+inline ScanFn scan_fn(int G, int mmax, bool tma, bool vec, bool lut = false) {
+  if (lut) return G == 4 ? scan_fn_lut_g4(mmax, tma, vec) : G == 8 ? scan_fn_lut_g8(mmax, tma, vec) : nullptr;
   switch (G) {
     case 4: return scan_fn_g4(mmax, tma, vec);
     case 8: return scan_fn_g8(mmax, tma, vec);

@@ -174,6 +174,7 @@ extern "C" int ihist_compute_noalloc(int h, int w, int nbins, int layout, const 
   f.H = h;
   f.W = w;
   f.B = nbins;
+  f.qmul = nbins;
   f.layout = layout;
   f.R = R;
   f.nbands = (h + R - 1) / R;

@@ -4,8 +4,10 @@
 // (Eq. 1 of arXiv 1711.01919), the result Algorithm 1 builds with its
 // recurrence, in one pass over the frame:
 //
-//   * a1 quantise: q = floor(v * B / 256) in registers; the paper's one-hot
-//     initialisation tensor (Alg. 2-4, step 1) is never materialised.
+//   * a1 quantise: q = floor(v * B / 256) in registers (or, for other bin
+//     structures, a 256-entry value -> bin table in shared memory); the
+//     paper's one-hot initialisation tensor (Alg. 2-4, step 1) is never
+//     materialised.
 //   * a2 row scan: per bin and row, a running count across the columns --
 //     4 columns per lane, then a warp shuffle scan over 128 columns with four
 //     bins packed in the bytes of one register, then a per-row carry from
@@ -43,7 +45,11 @@ struct FrameDesc {
   const uint8_t *in;
   long long pitch;      // bytes between rows of in
   uint32_t *out;
+  const uint32_t *lut;  // table kernels: 8 * bin of each intensity, or kNoBin (no bin)
   int H, W, B, layout;  // layout: 0 bin-major, 1 pixel-major
+  int qmul;             // uniform bins: q = (v * qmul) >> 8; qmul = B, or 256 when
+                        // the input already holds bin indices
+  int reserved_;
   int R, nbands, ngroups, nchunks, m;
   int wpg;              // warps per bin group: ceil(nchunks / m)
   int gpc;              // bin groups per CTA (warp w serves group w / wpg)
@@ -78,14 +84,23 @@ __host__ __device__ inline SmemLayout smem_layout(int NW, int R, int G, int nchu
   return L;
 }
 
-// Bit offset 8*q of the pixel's bin relative to the CTA's first bin
-// (gbase = 8 * g * G); an invalid column gets an offset that no sub-group
-// can match (shl_clamp gives 0).
-__device__ __forceinline__ uint32_t bin_offset(uint32_t v, uint32_t nbins, uint32_t gbase) {
-  return (((v * nbins) >> 8) << 3) - gbase;
-}
-
 constexpr uint32_t kNoBin = 0x80000000u;
+
+// a1: bit offset 8*q of a pixel's bin relative to the CTA's first bin
+// (gbase = 8 * g * G).  Offsets of bins outside the CTA's group, of values
+// in no bin and of columns past the frame are large or wrap around, so no
+// 4-bin sub-group matches them (shl_clamp gives 0).
+template <bool LUT>
+struct Binner {
+  uint32_t qmul;        // uniform: q = (v * qmul) >> 8
+  const uint32_t *lut;  // table: 8 * bin of each intensity (shared memory)
+  __device__ __forceinline__ uint32_t operator()(uint32_t v, uint32_t gbase) const {
+    if constexpr (LUT)
+      return lut[v] - gbase;
+    else
+      return (((v * qmul) >> 8) << 3) - gbase;
+  }
+};
 
 // Inclusive prefix of v[0..3] (this lane's 4 columns) over the 128-column chunk.
 __device__ __forceinline__ void chunk_scan32(uint32_t v[4], int lane) {
@@ -101,12 +116,13 @@ __device__ __forceinline__ void chunk_scan32(uint32_t v[4], int lane) {
 }
 
 // Bin offsets of this lane's 4 pixels in tile row yl (columns x .. x+3).
+template <bool LUT>
 __device__ __forceinline__ void tile_offsets(const uint8_t *tile, int yl, int lane, int x, int W,
-                                             uint32_t nbins, uint32_t gbase, uint32_t u[4]) {
+                                             const Binner<LUT> &bin, uint32_t gbase, uint32_t u[4]) {
   const uint32_t px = *reinterpret_cast<const uint32_t *>(tile + yl * kChunk + 4 * lane);
 #pragma unroll
   for (int i = 0; i < 4; ++i)
-    u[i] = (x + i < W) ? bin_offset(__byte_perm(px, 0u, 0x4440u + i), nbins, gbase) : kNoBin;
+    u[i] = (x + i < W) ? bin(__byte_perm(px, 0u, 0x4440u + i), gbase) : kNoBin;
 }
 
 // Stage rows y0 .. y0+nrows-1, columns c*128 .. c*128+127 of the frame into
@@ -151,12 +167,12 @@ __device__ __forceinline__ bool stage_tile(const FrameDesc &f, const CUtensorMap
 
 // ---------------------------------------------------------------------------
 // One work item: band k, bin group g.
-template <int G, int MMAX, bool TMA, bool VEC>
+template <int G, int MMAX, bool TMA, bool VEC, bool LUT>
 __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorMap *tmap,
                                              unsigned int it, uint32_t epoch, Ctrl *ctrl,
                                              unsigned long long timeout_ns, uint8_t *s_tiles,
                                              uint32_t *s_row, uint32_t *s_ctot, uint64_t *s_bar,
-                                             uint32_t &phase) {
+                                             const uint32_t *s_lut, uint32_t &phase) {
   constexpr int GQ = G / 4;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -168,7 +184,7 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
   const bool gvalid = (lg < f.gpc) && (g < f.ngroups);
   const int y0 = k * f.R;
   const int nrows = min(f.R, f.H - y0);
-  const uint32_t nbins = (uint32_t)f.B;
+  const Binner<LUT> bin{(uint32_t)f.qmul, s_lut};
   const uint32_t gbase = 8u * (uint32_t)(g * G);
   const int c_begin = wg * f.m;
   const int my_m = gvalid ? max(0, min(f.m, f.nchunks - c_begin)) : 0;  // warp-uniform
@@ -203,7 +219,7 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
 #pragma unroll 4
       for (int yl = 0; yl < nrows; ++yl) {
         uint32_t u[4];
-        tile_offsets(tile, yl, lane, x, f.W, nbins, gbase, u);
+        tile_offsets(tile, yl, lane, x, f.W, bin, gbase, u);
 #pragma unroll
         for (int q = 0; q < GQ; ++q) {
           uint32_t rs = 0u;
@@ -430,7 +446,7 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
       const bool last_chunk = (cc == my_m - 1);  // its row carries are not needed again
       for (int yl = 0; yl < nrows; ++yl) {
         uint32_t u[4];
-        tile_offsets(tile, yl, lane, x, f.W, nbins, gbase, u);
+        tile_offsets(tile, yl, lane, x, f.W, bin, gbase, u);
         uint32_t *rcp = myrow + (size_t)yl * G;
 #pragma unroll
         for (int q = 0; q < GQ; ++q) {
@@ -512,12 +528,13 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
 // belongs to a CTA that is already running; the last CTA to finish resets
 // the ticket and advances the epoch, so launches need no host-side reset
 // and can be captured in a CUDA graph.
-template <int G, int MMAX, bool TMA, bool VEC>
+template <int G, int MMAX, bool TMA, bool VEC, bool LUT>
 __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     scan_kernel(FrameDesc f, const __grid_constant__ CUtensorMap tmap, Ctrl *ctrl,
                 unsigned long long timeout_ns) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ unsigned int s_item, s_epoch;
+  __shared__ uint32_t s_lut[LUT ? 256 : 1];
   const int NW = blockDim.x >> 5;
   const SmemLayout L = smem_layout(NW, f.R, G, f.nchunks * f.gpc);
   uint8_t *base = reinterpret_cast<uint8_t *>(
@@ -529,6 +546,8 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (TMA && lane == 0) mbar_init(s_bar + w, 1);
   if (threadIdx.x == 0) s_epoch = *(volatile unsigned int *)&ctrl->epoch & 0x3fffffffu;
+  if (LUT)
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_lut[i] = __ldg(f.lut + i);
   if (TMA) mbar_init_fence();
   uint32_t phase = 0;
   for (;;) {
@@ -538,8 +557,8 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     const uint32_t epoch = s_epoch;
     __syncthreads();
     if (it >= f.nitems) break;
-    process_item<G, MMAX, TMA, VEC>(f, &tmap, it, epoch, ctrl, timeout_ns, s_tiles, s_row, s_ctot,
-                                    s_bar, phase);
+    process_item<G, MMAX, TMA, VEC, LUT>(f, &tmap, it, epoch, ctrl, timeout_ns, s_tiles, s_row, s_ctot,
+                                         s_bar, s_lut, phase);
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -608,8 +627,8 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     __syncthreads();
     if (t >= total) break;
     const unsigned int it = t - (fi > 0 ? ld_relaxed_u32(item_end + fi - 1) : 0u);
-    process_item<G, MMAX, TMA, VEC>(s_f, tmaps + fi, it, epoch, ctrl, timeout_ns, s_tiles, s_row,
-                                    s_ctot, s_bar, phase);
+    process_item<G, MMAX, TMA, VEC, false>(s_f, tmaps + fi, it, epoch, ctrl, timeout_ns, s_tiles, s_row,
+                                           s_ctot, s_bar, nullptr, phase);
     __syncthreads();
   }
   if (threadIdx.x == 0) {

@@ -7,8 +7,8 @@ namespace ihist {
 namespace {
 template <int MMAX>
 ScanFn pick(bool tma, bool vec) {
-  if (tma) return vec ? scan_kernel<16, MMAX, true, true> : scan_kernel<16, MMAX, true, false>;
-  return vec ? scan_kernel<16, MMAX, false, true> : scan_kernel<16, MMAX, false, false>;
+  if (tma) return vec ? scan_kernel<16, MMAX, true, true, false> : scan_kernel<16, MMAX, true, false, false>;
+  return vec ? scan_kernel<16, MMAX, false, true, false> : scan_kernel<16, MMAX, false, false, false>;
 }
 }  // namespace
 

@@ -34,7 +34,8 @@ EXPORTED = (
     "ihist_destroy", "ihist_error_string", "ihist_batch_plan", "ihist_batch_set_io",
     "ihist_batch_compute", "ihist_batch_query", "ihist_batch_status", "ihist_batch_workspace_bytes",
     "ihist_batch_items", "ihist_batch_destroy", "ihist_batch_query_all", "ihist_batch_upload_compute",
-    "ihist_compute_noalloc",
+    "ihist_compute_noalloc", "ihist_plan_lut", "ihist_plan_edges", "ihist_plan_joint",
+    "ihist_plan_channels",
 )
 
 
@@ -53,7 +54,8 @@ class ihist_tune_t(ctypes.Structure):
         ("timeout_us", ctypes.c_uint),
         ("fault_skip_band", ctypes.c_int),
         ("groups_per_cta", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("warps_per_cta", ctypes.c_int),
+        ("reserved", ctypes.c_int * 2),
     ]
 
 
@@ -70,7 +72,7 @@ class ihist_frame_t(ctypes.Structure):
 
 
 TUNE_FIELDS = ("rows_per_band", "bins_per_cta", "chunks_per_warp", "ctas_per_sm", "timeout_us",
-               "fault_skip_band", "groups_per_cta")
+               "fault_skip_band", "groups_per_cta", "warps_per_cta")
 
 _lock = threading.Lock()
 _lib = None
@@ -130,6 +132,16 @@ def load(path: str = LIB_PATH):
         L.ihist_batch_destroy.restype = None
         L.ihist_compute_noalloc.argtypes = [ci, ci, ci, ci, vp, sz, vp, vp, ctypes.POINTER(ci)]
         L.ihist_compute_noalloc.restype = ci
+        ip = ctypes.POINTER(ci)
+        tp = ctypes.POINTER(ihist_tune_t)
+        L.ihist_plan_lut.argtypes = [ci, ci, ci, ci, ip, tp, ctypes.POINTER(vp)]
+        L.ihist_plan_lut.restype = ci
+        L.ihist_plan_edges.argtypes = [ci, ci, ci, ci, ip, tp, ctypes.POINTER(vp)]
+        L.ihist_plan_edges.restype = ci
+        L.ihist_plan_joint.argtypes = [ci, ci, ci, ip, ci, tp, ctypes.POINTER(vp)]
+        L.ihist_plan_joint.restype = ci
+        L.ihist_plan_channels.argtypes = [vp]
+        L.ihist_plan_channels.restype = ci
         L.ihist_error_string.argtypes = [ci]
         L.ihist_error_string.restype = ctypes.c_char_p
         _lib = L
@@ -171,6 +183,47 @@ def ihist_plan_tuned(h: int, w: int, nbins: int, layout: int = IHIST_BIN_MAJOR, 
     _check(load().ihist_plan_tuned(h, w, nbins, layout, ctypes.byref(t), ctypes.byref(out)),
            "ihist_plan_tuned")
     return out.value
+
+
+def _ints(vals):
+    vals = [int(v) for v in vals]
+    return (ctypes.c_int * max(1, len(vals)))(*vals)
+
+
+def ihist_plan_lut(h: int, w: int, nbins: int, layout: int, bin_of_value, tune=None) -> int:
+    """Plan whose bins come from a 256-entry value -> bin map (-1 = no bin)."""
+    vals = list(bin_of_value)
+    if len(vals) != 256:
+        raise ValueError("bin_of_value must have 256 entries")
+    out = ctypes.c_void_p()
+    t = _tune_struct(tune) if tune else None
+    _check(load().ihist_plan_lut(h, w, nbins, layout, _ints(vals), ctypes.byref(t) if t else None,
+                                 ctypes.byref(out)), "ihist_plan_lut")
+    return out.value
+
+
+def ihist_plan_edges(h: int, w: int, layout: int, edges, tune=None) -> int:
+    """Plan with bins [edges[k], edges[k+1]); values outside count nowhere."""
+    e = list(edges)
+    out = ctypes.c_void_p()
+    t = _tune_struct(tune) if tune else None
+    _check(load().ihist_plan_edges(h, w, len(e) - 1, layout, _ints(e), ctypes.byref(t) if t else None,
+                                   ctypes.byref(out)), "ihist_plan_edges")
+    return out.value
+
+
+def ihist_plan_joint(h: int, w: int, bins_per_channel, layout: int = IHIST_BIN_MAJOR, tune=None) -> int:
+    """Plan for the joint bins of frames with len(bins_per_channel) interleaved channels."""
+    b = list(bins_per_channel)
+    out = ctypes.c_void_p()
+    t = _tune_struct(tune) if tune else None
+    _check(load().ihist_plan_joint(h, w, len(b), _ints(b), layout, ctypes.byref(t) if t else None,
+                                   ctypes.byref(out)), "ihist_plan_joint")
+    return out.value
+
+
+def ihist_plan_channels(plan: int) -> int:
+    return int(load().ihist_plan_channels(plan))
 
 
 def ihist_plan_get_tune(plan: int) -> dict:
@@ -300,15 +353,34 @@ class Plan:
     uint32 on the host: ``t.cpu().numpy().view(numpy.uint32)``).
     """
 
-    def __init__(self, h: int, w: int, nbins: int, layout: int = IHIST_BIN_MAJOR, tune=None):
+    def __init__(self, h: int, w: int, nbins: int = 0, layout: int = IHIST_BIN_MAJOR, tune=None,
+                 bin_of_value=None, edges=None, bins_per_channel=None):
         """tune: None (library defaults), a dict of ihist_tune_t fields, or
-        "auto" (measured by the autotuner, cached per device and shape)."""
+        "auto" (measured by the autotuner, cached per device and shape).
+        Binning: uniform over nbins bins by default; or bin_of_value (256
+        ints, -1 = no bin), or edges (nbins + 1 increasing ints in [0, 256]),
+        or bins_per_channel for the joint bins of multi-channel frames
+        ([h][w][C] uint8 tensors; nbins = the product)."""
+        if edges is not None:
+            nbins = len(edges) - 1
+        if bins_per_channel is not None:
+            nbins = 1
+            for b in bins_per_channel:
+                nbins *= int(b)
         self.h, self.w, self.nbins, self.layout = h, w, nbins, layout
+        self.channels = len(bins_per_channel) if bins_per_channel is not None else 1
         if tune == "auto":
             from . import autotune
             tune = autotune.tune_plan(h, w, nbins, layout)
-        self.handle = (ihist_plan_tuned(h, w, nbins, layout, tune) if tune
-                       else ihist_plan(h, w, nbins, layout))
+        if bin_of_value is not None:
+            self.handle = ihist_plan_lut(h, w, nbins, layout, bin_of_value, tune)
+        elif edges is not None:
+            self.handle = ihist_plan_edges(h, w, layout, edges, tune)
+        elif bins_per_channel is not None:
+            self.handle = ihist_plan_joint(h, w, bins_per_channel, layout, tune)
+        else:
+            self.handle = (ihist_plan_tuned(h, w, nbins, layout, tune) if tune
+                           else ihist_plan(h, w, nbins, layout))
         self.tune = ihist_plan_get_tune(self.handle)
 
     @property
@@ -322,11 +394,17 @@ class Plan:
         return torch.empty(self.out_shape, dtype=torch.int32, device=device or "cuda")
 
     def compute(self, frame, out=None, stream=None):
-        """Integral histogram of a CUDA uint8 [h][w] tensor (row stride may exceed w)."""
+        """Integral histogram of a CUDA uint8 [h][w] tensor (row stride may
+        exceed w), or [h][w][C] with interleaved channels for a joint plan."""
         import torch
-        if frame.dtype != torch.uint8 or frame.dim() != 2 or not frame.is_cuda:
+        if self.channels > 1 or frame.dim() == 3:
+            if (frame.dtype != torch.uint8 or frame.dim() != 3 or not frame.is_cuda
+                    or tuple(frame.shape) != (self.h, self.w, self.channels)
+                    or frame.stride(2) != 1 or frame.stride(1) != self.channels):
+                raise ValueError("frame must be a uint8 CUDA [h][w][C] tensor with interleaved channels")
+        elif frame.dtype != torch.uint8 or frame.dim() != 2 or not frame.is_cuda:
             raise ValueError("frame must be a 2-D uint8 CUDA tensor")
-        if tuple(frame.shape) != (self.h, self.w) or frame.stride(1) != 1:
+        elif tuple(frame.shape) != (self.h, self.w) or frame.stride(1) != 1:
             raise ValueError("frame shape/stride mismatch: %s %s" % (tuple(frame.shape), frame.stride()))
         if out is None:
             out = self.empty_output(frame.device)

@@ -21,6 +21,11 @@ compute.  Queries whose histogram is ready are launched as they come.
 Latency is taken from GPU event timestamps against a reference event
 recorded at the start, so it does not depend on how often the host polls.
 
+When only one frame is waiting, the batched server launches it alone
+(``ihist_compute`` with a per-shape plan): a one-frame batch only adds the
+descriptor upload.  Queries run on a stream of their own, so they do not
+queue behind frames that do not concern them.
+
 ``mode="plain"`` serves every frame with its own ``ihist_compute`` launch
 (no batching) -- the baseline the batched form is compared with.
 
@@ -216,15 +221,7 @@ class Server:
                     break
                 admit_frames.popleft()
                 ready_frames.append(r)
-            # 3. one batched launch of everything admitted (continuous batching)
-            while ready_frames:
-                batch, ready_frames = ready_frames[:self.max_batch], ready_frames[self.max_batch:]
-                h = self.ex.launch_frames(batch, t)
-                inflight.append((h, "frames", batch))
-                if self.mode != "batched":
-                    continue
-                break
-            # 4. queries whose histogram is ready
+            # 3. queries whose histogram is ready (first: they are short and wait on nothing)
             for _ in range(len(waiting_queries)):
                 q = waiting_queries.popleft()
                 if self.store.ready(q.target):
@@ -232,6 +229,14 @@ class Server:
                     inflight.append((h, "query", q))
                 else:
                     waiting_queries.append(q)
+            # 4. one batched launch of everything admitted (continuous batching)
+            while ready_frames:
+                batch, ready_frames = ready_frames[:self.max_batch], ready_frames[self.max_batch:]
+                h = self.ex.launch_frames(batch, t)
+                inflight.append((h, "frames", batch))
+                if self.mode != "batched":
+                    continue
+                break
             # 5. completions
             still = []
             for h, kind, obj in inflight:
@@ -301,9 +306,12 @@ class GpuExecutor:
     """Runs the server's launches with libihist on one GPU.
 
     batched: `nslots`-frame batch plans (two, alternating) whose slots are
-    sized for the largest frame of the mix; every launch rebinds the slots to
-    the admitted frames (ihist_batch_set_io) and uploads them on the copy
-    stream.  plain: one ihist_compute per frame with a plan per shape.
+    sized for the largest frame of the mix; every launch of two or more
+    frames rebinds the slots to the admitted frames (ihist_batch_set_io) and
+    uploads them on the copy stream; a single frame takes the plain path.
+    plain: one ihist_compute per frame with a plan per shape, its upload on
+    the copy stream into one of two staging buffers.  Queries: rectangles
+    up, Eq. 2 launch and rows back, all on a high-priority query stream.
     Output histograms come from torch's allocator on the compute stream and
     are returned to it on eviction.
     """
@@ -316,11 +324,13 @@ class GpuExecutor:
         self.mode = mode
         self.stream = torch.cuda.current_stream()
         self.copy = torch.cuda.Stream()
+        self.qstream = torch.cuda.Stream(priority=-1)
         self.s = self.stream.cuda_stream
         h, w, b = max_shape
         self.plans = {}
         self.batches = []
         self.inputs = []
+        self.inputs.append([torch.empty((h, w), dtype=torch.uint8, device="cuda") for _ in range(2)])
         if mode == "batched":
             for _ in range(2):
                 ins = [torch.empty((h, w), dtype=torch.uint8, device="cuda") for _ in range(nslots)]
@@ -328,8 +338,6 @@ class GpuExecutor:
                 self.batches.append(ihist.Batch(ins, b, outs=outs))
                 self.inputs.append(ins)
             del outs
-        else:
-            self.inputs.append([torch.empty((h, w), dtype=torch.uint8, device="cuda") for _ in range(2)])
         self.next_batch = 0
         self.next_input = 0
         self.read_done = [torch.cuda.Event() for _ in range(2)]
@@ -339,6 +347,12 @@ class GpuExecutor:
         self.t0_event = torch.cuda.Event(enable_timing=True)
         self.t0_wall = 0.0
         self.query_bufs = []
+
+    def warm(self, shapes):
+        """Create the per-shape plans before serving: plan creation allocates
+        and synchronises the device, which must not happen inside the loop."""
+        for (h, w, b) in shapes:
+            self._plan(h, w, b)
 
     def start(self):
         self.torch.cuda.synchronize()
@@ -359,9 +373,9 @@ class GpuExecutor:
         torch, ih = self.torch, self.ih
         outs = {r.rid: torch.empty((r.nbins, r.h, r.w), dtype=torch.int32, device="cuda") for r in reqs}
         ev = torch.cuda.Event(enable_timing=True)
-        if self.mode == "batched":
+        if self.mode == "batched" and len(reqs) > 1:
             b = self.batches[self.next_batch]
-            ins = self.inputs[self.next_batch]
+            ins = self.inputs[1 + self.next_batch]
             self.next_batch ^= 1
             views = [ins[i].view(-1)[:r.h * r.w].view(r.h, r.w) for i, r in enumerate(reqs)]
             b.set_io(views, [outs[r.rid] for r in reqs], nbins=[r.nbins for r in reqs],
@@ -385,17 +399,21 @@ class GpuExecutor:
         return {"ev": ev, "payloads": {r.rid: (outs[r.rid], r.h, r.w, r.nbins) for r in reqs}}
 
     def launch_query(self, q, payload, t):
+        # the server launches a query only once its histogram is complete,
+        # and keeps the histogram resident until the query is done
         torch = self.torch
         hist, h, w, b = payload
         rects = torch.from_numpy(np.ascontiguousarray(q.rects, dtype=np.int32)).pin_memory()
-        d_rects = torch.empty(rects.shape, dtype=torch.int32, device="cuda")
-        d_rects.copy_(rects, non_blocking=True)
-        out = torch.empty((rects.shape[0], b), dtype=torch.int32, device="cuda")
-        self._plan(h, w, b).query(hist, d_rects, out, stream=self.s)
-        host = torch.empty(out.shape, dtype=torch.int32).pin_memory()
-        host.copy_(out, non_blocking=True)
-        ev = torch.cuda.Event(enable_timing=True)
-        ev.record(self.stream)
+        with torch.cuda.stream(self.qstream):
+            d_rects = torch.empty(rects.shape, dtype=torch.int32, device="cuda")
+            d_rects.copy_(rects, non_blocking=True)
+            out = torch.empty((rects.shape[0], b), dtype=torch.int32, device="cuda")
+            self._plan(h, w, b).query(hist, d_rects, out, stream=self.qstream.cuda_stream)
+            host = torch.empty(out.shape, dtype=torch.int32).pin_memory()
+            host.copy_(out, non_blocking=True)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(self.qstream)
+        hist.record_stream(self.qstream)
         return {"ev": ev, "result": host, "keep": (rects, d_rects, out)}
 
     def poll(self, handle, t):
@@ -425,9 +443,11 @@ def serve(mode="batched", duration_s=2.0, budget_gb=40.0, seed=None, frame_rate=
                         for k in range(pool_per_shape)]
     reqs = serving_workload(seed, duration_s, frame_rate, query_rate, rects_per_query, pool)
     if saturate:
+        # the same requests, arriving 1000 times faster than the server can take them
         for r in reqs:
-            r.t_arrival = 0.0
+            r.t_arrival *= 1e-3
     ex = GpuExecutor(mode)
+    ex.warm(sorted({(r.h, r.w, r.nbins) for r in reqs if isinstance(r, FrameRequest)}))
     srv = Server(ex, int(budget_gb * (1 << 30)), mode=mode)
     ex.start()
     t0 = time.perf_counter()

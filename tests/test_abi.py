@@ -78,3 +78,23 @@ def test_plan_without_gpu_fails_cleanly(lib):
     with pytest.raises(ihist.IhistError) as e:
         ihist.ihist_plan(64, 64, 8, 0)
     assert e.value.code == ihist.IHIST_ERR_CUDA
+
+
+def test_other_bin_structures_reject_bad_arguments_before_touching_cuda(lib):
+    bad = [
+        (lambda: ihist.ihist_plan_edges(8, 8, 0, [10, 10, 20]), ihist.IHIST_ERR_INVALID_ARG),   # not increasing
+        (lambda: ihist.ihist_plan_edges(8, 8, 0, [-1, 20]), ihist.IHIST_ERR_INVALID_ARG),        # below 0
+        (lambda: ihist.ihist_plan_edges(8, 8, 0, [0, 257]), ihist.IHIST_ERR_INVALID_ARG),        # above 256
+        (lambda: ihist.ihist_plan_lut(8, 8, 4, 0, [4] * 256), ihist.IHIST_ERR_INVALID_ARG),      # bin >= nbins
+        (lambda: ihist.ihist_plan_lut(8, 8, 4, 0, [-2] * 256), ihist.IHIST_ERR_INVALID_ARG),     # below -1
+        (lambda: ihist.ihist_plan_lut(8, 8, 4, 0, [0] * 256, {"bins_per_cta": 16}), ihist.IHIST_ERR_UNSUPPORTED),
+        (lambda: ihist.ihist_plan_joint(8, 8, [8, 8, 8]), ihist.IHIST_ERR_UNSUPPORTED),         # 512 joint bins
+        (lambda: ihist.ihist_plan_joint(8, 8, [2, 0]), ihist.IHIST_ERR_INVALID_ARG),
+        (lambda: ihist.ihist_plan_joint(8, 8, [2] * 5), ihist.IHIST_ERR_INVALID_ARG),           # 5 channels
+        (lambda: ihist.ihist_plan_joint(8, 20000, [2, 2, 2, 2]), ihist.IHIST_ERR_UNSUPPORTED),  # w * C too wide
+    ]
+    for make, code in bad:
+        with pytest.raises(ihist.IhistError) as e:
+            make()
+        assert e.value.code == code
+    assert ihist.ihist_plan_channels(None) == 0

@@ -39,9 +39,14 @@ def test_search_picks_fastest_and_skips_rejected(tmp_path, monkeypatch):
 def test_batch_tuning_key_and_cache(tmp_path, monkeypatch):
     monkeypatch.setenv("IHIST_TUNE_CACHE", str(tmp_path / "c.json"))
     shapes = [(240, 320, 16, 0), (1080, 1920, 64, 0), (240, 320, 16, 0)]
-    best = autotune.tune_batch(shapes, timer=lambda t: abs(t.get("rows_per_band", 0) - 40) + 0.5 * (t.get("bins_per_cta", 4) == 8),
-                               device="fake")
-    assert best == {"bins_per_cta": 4, "rows_per_band": 40}
+    def timer(t):
+        if t.get("warps_per_cta") == 8 and t.get("rows_per_band") == 56:
+            raise ihist.IhistError(ihist.IHIST_ERR_UNSUPPORTED, "batch")
+        return (abs(t.get("rows_per_band", 0) - 40) + 0.5 * (t.get("bins_per_cta", 4) == 8)
+                + 0.25 * (t.get("warps_per_cta", 16) == 16))
+
+    best = autotune.tune_batch(shapes, timer=timer, device="fake")
+    assert best == {"warps_per_cta": 8, "bins_per_cta": 4, "rows_per_band": 40}
     cache = json.load(open(tmp_path / "c.json"))
     assert any(k.startswith("batch|fake|3|") for k in cache)
 

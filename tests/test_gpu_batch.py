@@ -41,7 +41,8 @@ MIXED = [(1, 1, 1, 0), (5, 3, 3, 1), (37, 131, 16, 0), (240, 320, 16, 0), (64, 2
 
 
 @pytest.mark.parametrize("tune", [None, {"rows_per_band": 8}, {"rows_per_band": 64, "bins_per_cta": 8},
-                                  {"rows_per_band": 3, "ctas_per_sm": 1}])
+                                  {"rows_per_band": 3, "ctas_per_sm": 1}, {"warps_per_cta": 8},
+                                  {"warps_per_cta": 8, "bins_per_cta": 8, "rows_per_band": 40}])
 def test_mixed_batch(tune):
     imgs = [synth.uniform_frame(1000 + i, h, w) for i, (h, w, b, l) in enumerate(MIXED)]
     nbins = [b for (h, w, b, l) in MIXED]
@@ -202,3 +203,24 @@ def test_set_io_narrower_frames_keep_the_planned_launch_shape():
             batch.compute()
             assert batch.status() == ihist.IHIST_OK
             check_batch(batch, imgs, [b for (h, w, b) in shapes], [0, 0])
+
+
+def test_warps_per_cta_4_and_too_wide_frames_are_rejected():
+    # 4-warp CTAs: 300x4096 needs 32 chunks = 8 per warp > 4, so the plan is refused
+    small = [(37, 131, 16, 0), (240, 320, 16, 0), (64, 257, 7, 1), (100, 1000, 64, 1)]
+    imgs = [synth.uniform_frame(2000 + i, h, w) for i, (h, w, b, l) in enumerate(small)]
+    nbins = [b for (h, w, b, l) in small]
+    layouts = [l for (h, w, b, l) in small]
+    with ihist.Batch([torch.from_numpy(x).cuda() for x in imgs], nbins, layouts,
+                     tune={"warps_per_cta": 4}) as batch:
+        batch.compute()
+        assert batch.status() == ihist.IHIST_OK
+        check_batch(batch, imgs, nbins, layouts)
+    wide = [torch.zeros((300, 4096), dtype=torch.uint8, device="cuda")]
+    with pytest.raises(ihist.IhistError) as e:
+        ihist.Batch(wide, [8], tune={"warps_per_cta": 4})
+    assert e.value.code == ihist.IHIST_ERR_UNSUPPORTED
+    # 16-warp CTAs reach 16 x 4 chunks = 8192 columns; wider frames are refused
+    with pytest.raises(ihist.IhistError) as e:
+        ihist.Batch([torch.zeros((16, 9000), dtype=torch.uint8, device="cuda")], [8])
+    assert e.value.code == ihist.IHIST_ERR_UNSUPPORTED
