@@ -70,6 +70,7 @@ class Done:
     t_done: float
     status: str = "ok"        # ok | rejected
     target: int = -1
+    t_launch: float = -1.0    # host time of the launch that served it
 
 
 def hist_bytes(h: int, w: int, nbins: int) -> int:
@@ -180,6 +181,7 @@ class Server:
         self.rng = np.random.default_rng(seed)
         self.done = []
         self.results = {}
+        self.batch_sizes = collections.Counter()
 
     def run(self, requests, clock, max_wall: float = 600.0):
         """Serve `requests` (sorted by t_arrival).  clock() returns seconds since
@@ -226,6 +228,7 @@ class Server:
                 q = waiting_queries.popleft()
                 if self.store.ready(q.target):
                     h = self.ex.launch_query(q, self.store.payload(q.target), t)
+                    h["t_launch"] = clock()
                     inflight.append((h, "query", q))
                 else:
                     waiting_queries.append(q)
@@ -233,6 +236,8 @@ class Server:
             while ready_frames:
                 batch, ready_frames = ready_frames[:self.max_batch], ready_frames[self.max_batch:]
                 h = self.ex.launch_frames(batch, t)
+                h["t_launch"] = clock()
+                self.batch_sizes[len(batch)] += 1
                 inflight.append((h, "frames", batch))
                 if self.mode != "batched":
                     continue
@@ -246,28 +251,33 @@ class Server:
                         for r in obj:
                             self.store.set_ready(r.rid, h["payloads"][r.rid])
                             self.store.touch(r.rid)
-                            self.done.append(Done(r.rid, "frame", r.t_arrival, td))
+                            self.done.append(Done(r.rid, "frame", r.t_arrival, td, t_launch=h["t_launch"]))
                     else:
                         self.store.unpin(obj.target)
                         self.store.touch(obj.target)
                         self.results[obj.rid] = h.get("result")
-                        self.done.append(Done(obj.rid, "query", obj.t_arrival, td, target=obj.target))
+                        self.done.append(Done(obj.rid, "query", obj.t_arrival, td, target=obj.target,
+                                              t_launch=h["t_launch"]))
                 else:
                     still.append((h, kind, obj))
             inflight = still
         return self.done
 
     def report(self, wall_s: float):
-        out = {"mode": self.mode, "evicted": self.store.evicted}
+        out = {"mode": self.mode, "evicted": self.store.evicted,
+               "launch_sizes": {str(k): v for k, v in sorted(self.batch_sizes.items())}}
         for kind in ("frame", "query"):
             ok = [d for d in self.done if d.kind == kind and d.status == "ok"]
             lat = np.array([d.t_done - d.t_arrival for d in ok]) * 1e3
+            wait = np.array([d.t_launch - d.t_arrival for d in ok]) * 1e3  # host: arrival -> launched
             out[kind] = {
                 "completed": len(ok),
                 "rejected": sum(1 for d in self.done if d.kind == kind and d.status != "ok"),
                 "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
                 "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
                 "max_ms": float(lat.max()) if len(lat) else None,
+                "launch_wait_p50_ms": float(np.percentile(wait, 50)) if len(wait) else None,
+                "launch_wait_p99_ms": float(np.percentile(wait, 99)) if len(wait) else None,
                 "per_s": len(ok) / wall_s if wall_s > 0 else None,
             }
         return out
