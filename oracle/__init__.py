@@ -23,6 +23,9 @@ integral_histogram_mapped(img, bin_map, nbins)   Algorithm 1 for any value -> bi
 integral_histogram_edges(img, edges)             Algorithm 1 for bins given by edges.
 integral_histogram_joint(img, bins)              Algorithm 1 over the joint bins of a
                                   [h][w][C] frame (channel 0 most significant).
+window_intersection(img, nbins, target, win_h, win_w, stride)
+                                  histogram-intersection score of every window on a
+                                  stride grid, each window counted directly.
 
 ``Oracle(path)`` wraps any shared object built from ``ihist_oracle.c``; the
 tests use it to load deliberately mutated copies and check that the pins
@@ -112,6 +115,10 @@ class Oracle:
         lib.oracle_ih_joint.argtypes = [_u8p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         _i32p, _u32p]
         lib.oracle_ih_joint.restype = None
+        lib.oracle_window_intersection.argtypes = [_u8p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, _u32p, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, _u32p]
+        lib.oracle_window_intersection.restype = None
         self.lib = lib
         self.path = path
 
@@ -213,6 +220,21 @@ class Oracle:
             self.lib.oracle_ih_joint(_p8(a), a.strides[0], h, w, c, b.ctypes.data_as(_i32p), _p32(out))
         return out
 
+    def window_intersection(self, img, nbins: int, target, win_h: int, win_w: int, stride: int) -> np.ndarray:
+        """[ny][nx] uint32 scores sum_b min(window count_b, target_b)."""
+        a = _img(img)
+        h, w = a.shape
+        if not (1 <= win_h <= h and 1 <= win_w <= w and stride >= 1):
+            raise ValueError("window must fit the frame and stride must be >= 1")
+        t = np.ascontiguousarray(np.asarray(target, dtype=np.uint32))
+        if t.shape != (nbins,):
+            raise ValueError("target must hold nbins counts")
+        ny, nx = (h - win_h) // stride + 1, (w - win_w) // stride + 1
+        out = np.zeros((ny, nx), dtype=np.uint32)
+        self.lib.oracle_window_intersection(_p8(a), a.strides[0], h, w, nbins, _p32(t), win_h, win_w, stride,
+                                            _p32(out))
+        return out
+
 
 def default() -> Oracle:
     """The oracle built from ihist_oracle.c as committed."""
@@ -261,3 +283,7 @@ def integral_histogram_edges(img, edges, out=None):
 
 def integral_histogram_joint(img, bins, out=None):
     return default().integral_histogram_joint(img, bins, out)
+
+
+def window_intersection(img, nbins, target, win_h, win_w, stride):
+    return default().window_intersection(img, nbins, target, win_h, win_w, stride)

@@ -180,6 +180,37 @@ void oracle_ih_joint(const uint8_t *img, size_t pitch, int h, int w,
   }
 }
 
+/* ---- a consumer of the integral histogram: sliding-window search -------
+ *
+ * Detection and tracking compare the histogram of every candidate window
+ * with a target histogram (Sec. 1), which is what the O(1) region query is
+ * for.  Readings taken here: windows of win_h x win_w pixels whose top-left
+ * corners lie on the grid (i * stride, j * stride), i = 0 .. ny-1,
+ * j = 0 .. nx-1, ny = (h - win_h) / stride + 1, nx = (w - win_w) / stride + 1
+ * (integer division: only windows inside the frame); the score of a window
+ * is the histogram intersection sum_b min(count_b, target_b) of Swain and
+ * Ballard (1991), an exact integer.  This oracle counts each window's pixels
+ * directly, without Eq. 2. */
+void oracle_window_intersection(const uint8_t *img, size_t pitch, int h, int w, int nbins,
+                                const uint32_t *target, int win_h, int win_w, int stride,
+                                uint32_t *out) {
+  const int ny = (h - win_h) / stride + 1, nx = (w - win_w) / stride + 1;
+  uint32_t *count = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)nbins);
+  if (!count) return;
+  for (int i = 0; i < ny; ++i) {
+    for (int j = 0; j < nx; ++j) {
+      for (int b = 0; b < nbins; ++b) count[b] = 0u;
+      for (int r = i * stride; r < i * stride + win_h; ++r)
+        for (int c = j * stride; c < j * stride + win_w; ++c)
+          count[oracle_bin_of(img[(size_t)r * pitch + c], nbins)] += 1u;
+      uint32_t score = 0u;
+      for (int b = 0; b < nbins; ++b) score += count[b] < target[b] ? count[b] : target[b];
+      out[(size_t)i * nx + j] = score;
+    }
+  }
+  free(count);
+}
+
 /* ---- bins-parallel variant, for timing the CPU on all host cores ------ */
 
 typedef struct {

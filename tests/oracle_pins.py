@@ -398,5 +398,37 @@ def check_joint(o) -> None:
     assert np.array_equal(o.integral_histogram_joint(img, cbins), brute_from_bins(bins, 24))
 
 
+def numpy_window_intersection(img, nbins, target, win_h, win_w, stride):
+    """Window counts by numpy's sliding_window_view over the one-hot planes."""
+    onehot = (binned(img, nbins)[None, :, :] == np.arange(nbins)[:, None, None]).astype(np.int64)
+    win = np.lib.stride_tricks.sliding_window_view(onehot, (win_h, win_w), axis=(1, 2))[:, ::stride, ::stride]
+    counts = win.sum(axis=(-1, -2))
+    return np.minimum(counts, np.asarray(target, dtype=np.int64)[:, None, None]).sum(axis=0)
+
+
+def check_window_search(o) -> None:
+    """Sliding-window histogram intersection: numpy windows, closed forms, self-match."""
+    rng = np.random.default_rng(99)
+    for (h, w, nbins, wh, ww, st) in [(20, 31, 8, 5, 7, 1), (33, 40, 16, 8, 8, 3), (16, 16, 4, 16, 16, 5),
+                                      (9, 50, 32, 1, 1, 2), (30, 30, 3, 7, 4, 4)]:
+        img = rng.integers(0, 256, size=(h, w), dtype=np.uint8)
+        target = rng.integers(0, wh * ww + 1, size=nbins)
+        got = o.window_intersection(img, nbins, target, wh, ww, st)
+        exp = numpy_window_intersection(img, nbins, target, wh, ww, st)
+        assert got.shape == ((h - wh) // st + 1, (w - ww) // st + 1), (h, w, wh, ww, st)
+        assert np.array_equal(got.astype(np.int64), exp), (h, w, nbins, wh, ww, st)
+    # constant frame: every window holds area pixels of one bin
+    img = np.full((12, 17), 200, dtype=np.uint8)
+    target = np.arange(8) * 3
+    got = o.window_intersection(img, 8, target, 4, 5, 2)
+    assert (got == min(20, int(target[brute_bin(200, 8)]))).all()
+    # the target taken from one window scores that window's full area there and no more anywhere
+    img = rng.integers(0, 256, size=(24, 24), dtype=np.uint8)
+    target = brute_region(img, 6, (8, 4, 15, 11)).astype(np.int64)  # window at row 4, col 8
+    got = o.window_intersection(img, 6, target, 8, 8, 4)
+    assert got[1, 2] == 64 and got.max() == 64
+
+
 ALL_CHECKS = (check_bins, check_golden, check_brute_force, check_invariants,
-              check_closed_forms, check_query, check_threads, check_edges, check_mapped, check_joint)
+              check_closed_forms, check_query, check_threads, check_edges, check_mapped, check_joint,
+              check_window_search)

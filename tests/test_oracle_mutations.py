@@ -35,6 +35,15 @@ MUTATIONS = [
     ("joint_radix", "k = k * bins[c] + oracle_bin_of(px[c], bins[c]);",
      "k = k + oracle_bin_of(px[c], bins[c]) * (c ? bins[c - 1] : 1);"),
     ("joint_pixel_stride", "img + (size_t)x * pitch + (size_t)y * channels;", "img + (size_t)x * pitch + (size_t)y;"),
+    ("window_short_rows", "for (int r = i * stride; r < i * stride + win_h; ++r)",
+     "for (int r = i * stride; r < i * stride + win_h - 1; ++r)"),
+    # (each mutant below still reads and writes only inside its buffers)
+    ("window_square_assumed", "for (int r = i * stride; r < i * stride + win_h; ++r)",
+     "for (int r = i * stride; r < i * stride + (win_w < win_h ? win_w : win_h); ++r)"),
+    ("window_max_not_min", "score += count[b] < target[b] ? count[b] : target[b];",
+     "score += count[b] > target[b] ? count[b] : target[b];"),
+    ("window_row_step", "for (int r = i * stride; r < i * stride + win_h; ++r)",
+     "for (int r = i * (stride - (stride > 1)); r < i * (stride - (stride > 1)) + win_h; ++r)"),
 ]
 
 
