@@ -346,7 +346,89 @@ def configs_report(stream, peak: float) -> dict:
                                       "query_ms_2p20_rects": qms, "tile": plan.tune}
     del img, out, rects, q
     torch.cuda.empty_cache()
+    rep["host_output_1080p_b64"] = host_output_report(stream, peak)
+    rep["window_search_1080p_b64"] = window_search_report(stream)
+    rep["paper_mappings_1080p_b64"] = mappings_report(stream, peak)
     return rep
+
+
+def mappings_report(stream, peak: float) -> dict:
+    """The paper's GPU mappings (CW-STS, CW-TiS, WF-TiS; comparison kernels
+    built on this GPU) against the fused look-back kernel, one 1080p frame
+    with 64 bins each, same output, same algorithmic bytes."""
+    import torch
+
+    from paper_1711_01919_gb300 import ihist, synth
+    s = stream.cuda_stream
+    img = torch.from_numpy(synth.gradient_frame(synth.workload_seed(2), H, W)).cuda()
+    out = torch.empty((NBINS, H, W), dtype=torch.int32, device="cuda")
+    byts = algorithmic_bytes_per_frame()
+    rep = {}
+    for name, m in ihist.MAPPINGS.items():
+        nb = ihist.ihist_mapping_workspace_bytes(m, H, W, NBINS)
+        work = torch.empty((max(nb, 1),), dtype=torch.uint8, device="cuda")
+        ms = _median_ms(lambda: ihist.ihist_mapping_compute(m, H, W, NBINS, img.data_ptr(), W, out.data_ptr(),
+                                                            work.data_ptr() if nb else 0, s), stream)
+        rep[name] = {"ms_per_frame": ms, "frames_per_s": 1e3 / ms, "frac": byts / ms / 1e6 / peak}
+        del work
+    with ihist.Plan(H, W, NBINS) as plan:
+        ms = _median_ms(lambda: ihist.ihist_compute(plan.handle, img.data_ptr(), W, out.data_ptr(), s), stream)
+    rep["fused_look_back"] = {"ms_per_frame": ms, "frames_per_s": 1e3 / ms, "frac": byts / ms / 1e6 / peak}
+    return rep
+
+
+def window_search_report(stream) -> dict:
+    """Sliding-window search over one resident 1080p histogram (64 bins):
+    64x64 windows every 4 pixels (255 x 465 = 118,575 windows), each scored
+    by histogram intersection with a target from Eq. 2's four lookups per
+    bin, for both layouts of H."""
+    import torch
+
+    from paper_1711_01919_gb300 import ihist, synth
+    img = synth.gradient_frame(synth.workload_seed(2), H, W)
+    d = torch.from_numpy(img).cuda()
+    target = torch.from_numpy(np.bincount(((img[500:564, 900:964].astype(np.int64) * NBINS) >> 8).ravel(),
+                                          minlength=NBINS).astype(np.int32)).cuda()
+    out = {}
+    for name, layout in (("bin_major", ihist.IHIST_BIN_MAJOR), ("pixel_major", ihist.IHIST_PIXEL_MAJOR)):
+        with ihist.Plan(H, W, NBINS, layout) as plan:
+            hist = plan.compute(d)
+            scores = plan.window_search(hist, target, 64, 64, 4)
+            ms = _median_ms(lambda: plan.window_search(hist, target, 64, 64, 4, out=scores), stream)
+            if plan.status() != ihist.IHIST_OK:
+                raise SystemExit("device status error in the window search")
+            n = scores.numel()
+            out[name] = {"ms": ms, "windows": n, "windows_per_s": n / ms * 1e3,
+                         "corner_gbs": n * 4 * NBINS * 4 / ms / 1e6}
+        del hist
+    return out
+
+
+def host_output_report(stream, peak: float, n: int = 16) -> dict:
+    """Stand-alone mode: the integral histogram of each 1080p frame written
+    straight into page-locked host memory by the scan kernel (its stores
+    cross the CPU-GPU link; no device copy of H, no separate transfer),
+    against the rate of a plain device-to-host copy of the same bytes."""
+    import torch
+
+    from paper_1711_01919_gb300 import ihist, synth
+    s = stream.cuda_stream
+    seed = synth.workload_seed(2)
+    fr = [torch.from_numpy(synth.gradient_frame(synth.substream_seed(seed, i), H, W)).cuda() for i in range(4)]
+    host = [torch.empty((NBINS, H, W), dtype=torch.int32).pin_memory() for _ in range(2)]
+    dev = torch.empty((NBINS, H, W), dtype=torch.int32, device="cuda")
+    nb = H * W * NBINS * 4
+    with ihist.Plan(H, W, NBINS) as plan:
+        def run():
+            for i in range(n):
+                ihist.ihist_compute(plan.handle, fr[i % 4].data_ptr(), W, host[i % 2].data_ptr(), s)
+        ms = _median_ms(run, stream, reps=3, warm=1) / n
+        if plan.status() != ihist.IHIST_OK:
+            raise SystemExit("device status error in the host-output run")
+    copy_ms = _median_ms(lambda: host[0].copy_(dev, non_blocking=True), stream, reps=3, warm=1)
+    return {"frames_per_s": 1e3 / ms, "ms_per_frame": ms, "link_gbs": nb / ms / 1e6,
+            "d2h_copy_gbs": nb / copy_ms / 1e6, "frac_of_d2h_copy": copy_ms / ms,
+            "form": "ihist_compute with d_out in page-locked host memory (bin-major)"}
 
 
 def other_bins_report(d_frames, outs, stream, steps: int = 5) -> dict:

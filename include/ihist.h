@@ -155,10 +155,19 @@ size_t ihist_output_bytes(int h, int w, int nbins);
 
 /* Integral histogram of one frame (Eq. 1; fused quantise, row scan, column
  * scan and carry passing).  d_in: h rows of w bytes (w * channels for a
- * joint plan), row stride in_pitch (>= that) bytes.  d_out: ihist_output_bytes(h, w, nbins) bytes in the plan's
- * layout; every word is written exactly once.  The fast path wants d_in and
- * in_pitch 4-byte aligned and d_out 16-byte aligned with w % 4 == 0;
- * anything else takes a slower element-wise path with the same result. */
+ * joint plan), row stride in_pitch (>= that) bytes.  d_out:
+ * ihist_output_bytes(h, w, nbins) bytes in the plan's layout; every word is
+ * written exactly once.  The fast path wants d_in and in_pitch 4-byte
+ * aligned and d_out 16-byte aligned with w % 4 == 0; anything else takes a
+ * slower element-wise path with the same result.
+ * Stand-alone use (results wanted in host memory, Alg. 6's copy back,
+ * Sec. 4.3-4.4): d_out may be page-locked host memory the device can address
+ * (cudaHostAlloc, or cudaHostRegister'ed with mapping).  The kernel's stores
+ * then cross the CPU-GPU link themselves, so no device copy of H and no
+ * separate transfer is needed; the frame rate is that of the link (on a
+ * GB300 about the same as a device-to-host copy of the same bytes).  Use
+ * the bin-major layout there: pixel-major stores are too scattered for the
+ * link.  The caller synchronises `stream` before reading d_out on the host. */
 int ihist_compute(ihist_plan_t plan, const uint8_t *d_in, size_t in_pitch, uint32_t *d_out,
                   void *stream);
 
@@ -169,6 +178,44 @@ int ihist_compute(ihist_plan_t plan, const uint8_t *d_in, size_t in_pitch, uint3
  * zero row and latches IHIST_ERR_BAD_RECT.  n == 0 is a no-op. */
 int ihist_query(ihist_plan_t plan, const uint32_t *d_hist, const int32_t *d_rects, int n,
                 uint32_t *d_hist_out, void *stream);
+
+/* Sliding-window histogram search over a resident integral histogram (the
+ * detection / tracking use of Sec. 1).  Window (i, j) covers rows
+ * i*stride .. i*stride + win_h - 1 and columns j*stride .. j*stride + win_w - 1
+ * for i < ny = (h - win_h) / stride + 1 and j < nx = (w - win_w) / stride + 1
+ * (only windows inside the frame).  Its histogram comes from Eq. 2 and its
+ * score is the histogram intersection sum_b min(h_b, target_b), an exact
+ * integer <= win_h * win_w.
+ *   d_hist    an integral histogram made with this plan's shape and layout
+ *             (pixel-major reads each corner as one contiguous vector and is
+ *             the faster layout here)
+ *   d_target  nbins uint32 counts, device
+ *   d_scores  ny * nx uint32, row-major [i][j], device
+ * IHIST_ERR_INVALID_ARG if the window does not fit the frame or stride < 1.
+ * Asynchronous on stream; allocates nothing. */
+int ihist_window_search(ihist_plan_t plan, const uint32_t *d_hist, const uint32_t *d_target, int win_h,
+                        int win_w, int stride, uint32_t *d_scores, void *stream);
+
+/* The paper's own GPU mappings, rebuilt on this GPU as comparison kernels
+ * for measuring the fused look-back design against them (not a fast path):
+ *   IHIST_MAPPING_CW_STS  Sec. 3.3 / Alg. 3: one-hot tensor, one row-scan
+ *                         launch, 3-D transpose, row scan, transpose back
+ *   IHIST_MAPPING_CW_TIS  Sec. 3.4 / Alg. 4: one-hot tensor, a launch per
+ *                         vertical strip of 32-column tiles (row scans),
+ *                         then a launch per horizontal strip (column scans)
+ *   IHIST_MAPPING_WF_TIS  Sec. 3.5 / Alg. 5 / Eq. 6: one-hot tensor, then a
+ *                         launch per anti-diagonal of 32 x 32 tiles, each
+ *                         tile scanned in shared memory and offset by the
+ *                         final column to its left and row above
+ * All three write exactly the H of Eq. 1, bin-major, into d_out (which also
+ * holds the one-hot tensor while they run).  d_work: a device buffer of
+ * ihist_mapping_workspace_bytes() bytes (0, and d_work may be NULL, for
+ * the tiled mappings).  Shape limits as ihist_plan; asynchronous on stream.
+ * IHIST_ERR_INVALID_ARG for an unknown mapping or a bad shape or pointer. */
+enum { IHIST_MAPPING_CW_STS = 1, IHIST_MAPPING_CW_TIS = 2, IHIST_MAPPING_WF_TIS = 3 };
+size_t ihist_mapping_workspace_bytes(int mapping, int h, int w, int nbins);
+int ihist_mapping_compute(int mapping, int h, int w, int nbins, const uint8_t *d_in, size_t in_pitch,
+                          uint32_t *d_out, void *d_work, void *stream);
 
 /* A sequence of frames from HOST memory (the dual-buffered pipeline of
  * Algorithm 6, Sec. 4.4): frame i+1 is uploaded on copy_stream into one of

@@ -16,6 +16,7 @@
 #include "ihist_joint.cuh"
 #include "ihist_kernels.h"
 #include "ihist_query.cuh"
+#include "ihist_window.cuh"
 
 using namespace ihist;
 
@@ -517,6 +518,34 @@ extern "C" int ihist_query(ihist_plan_t p, const uint32_t *d_hist, const int32_t
   if (rc != IHIST_OK) return rc;
   return launch_query(p->H, p->W, p->B, p->layout, p->sms, p->ctrl, d_hist, d_rects, n, d_hist_out,
                       stream);
+}
+
+extern "C" int ihist_window_search(ihist_plan_t p, const uint32_t *d_hist, const uint32_t *d_target, int win_h,
+                                   int win_w, int stride, uint32_t *d_scores, void *stream) {
+  if (!p || !d_hist || !d_target || !d_scores) return IHIST_ERR_INVALID_ARG;
+  if (win_h < 1 || win_w < 1 || win_h > p->H || win_w > p->W || stride < 1) return IHIST_ERR_INVALID_ARG;
+  if (((uintptr_t)d_hist & 3u) || ((uintptr_t)d_target & 3u) || ((uintptr_t)d_scores & 3u))
+    return IHIST_ERR_INVALID_ARG;
+  int rc = check_device(p);
+  if (rc != IHIST_OK) return rc;
+  const int ny = (p->H - win_h) / stride + 1, nx = (p->W - win_w) / stride + 1;
+  const long long total = (long long)ny * nx;
+  const unsigned int threads = 256;
+  const size_t smem = (size_t)p->B * sizeof(uint32_t);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->layout == IHIST_BIN_MAJOR) {
+    const unsigned int grid =
+        (unsigned int)std::min<long long>((total + threads - 1) / threads, (long long)p->sms * 8);
+    window_kernel_bin_major<<<grid, threads, smem, s>>>(d_hist, p->H, p->W, p->B, d_target, win_h, win_w, stride,
+                                                        ny, nx, d_scores);
+  } else {
+    const unsigned int grid =
+        (unsigned int)std::min<long long>((total + threads / 32 - 1) / (threads / 32), (long long)p->sms * 8);
+    window_kernel_pixel_major<<<grid, threads, smem, s>>>(d_hist, p->H, p->W, p->B, d_target, win_h, win_w,
+                                                          stride, ny, nx, d_scores);
+  }
+  if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
+  return IHIST_OK;
 }
 
 extern "C" int ihist_sequence_host(ihist_plan_t p, const uint8_t *h_frames, size_t frame_stride,

@@ -35,7 +35,7 @@ EXPORTED = (
     "ihist_batch_compute", "ihist_batch_query", "ihist_batch_status", "ihist_batch_workspace_bytes",
     "ihist_batch_items", "ihist_batch_destroy", "ihist_batch_query_all", "ihist_batch_upload_compute",
     "ihist_compute_noalloc", "ihist_plan_lut", "ihist_plan_edges", "ihist_plan_joint",
-    "ihist_plan_channels",
+    "ihist_plan_channels", "ihist_window_search", "ihist_mapping_workspace_bytes", "ihist_mapping_compute",
 )
 
 
@@ -140,6 +140,12 @@ def load(path: str = LIB_PATH):
         L.ihist_plan_edges.restype = ci
         L.ihist_plan_joint.argtypes = [ci, ci, ci, ip, ci, tp, ctypes.POINTER(vp)]
         L.ihist_plan_joint.restype = ci
+        L.ihist_mapping_workspace_bytes.argtypes = [ci, ci, ci, ci]
+        L.ihist_mapping_workspace_bytes.restype = sz
+        L.ihist_mapping_compute.argtypes = [ci, ci, ci, ci, vp, sz, vp, vp, vp]
+        L.ihist_mapping_compute.restype = ci
+        L.ihist_window_search.argtypes = [vp, vp, vp, ci, ci, ci, vp, vp]
+        L.ihist_window_search.restype = ci
         L.ihist_plan_channels.argtypes = [vp]
         L.ihist_plan_channels.restype = ci
         L.ihist_error_string.argtypes = [ci]
@@ -242,6 +248,32 @@ def ihist_compute(plan: int, d_in: int, in_pitch: int, d_out: int, stream: int =
 
 def ihist_query(plan: int, d_hist: int, d_rects: int, n: int, d_hist_out: int, stream: int = 0) -> None:
     _check(load().ihist_query(plan, d_hist, d_rects, n, d_hist_out, stream), "ihist_query")
+
+
+def ihist_window_search(plan: int, d_hist: int, d_target: int, win_h: int, win_w: int, stride: int,
+                        d_scores: int, stream: int = 0) -> None:
+    _check(load().ihist_window_search(plan, d_hist, d_target, win_h, win_w, stride, d_scores, stream),
+           "ihist_window_search")
+
+
+IHIST_MAPPING_CW_STS, IHIST_MAPPING_CW_TIS, IHIST_MAPPING_WF_TIS = 1, 2, 3
+MAPPINGS = {"cw_sts": IHIST_MAPPING_CW_STS, "cw_tis": IHIST_MAPPING_CW_TIS, "wf_tis": IHIST_MAPPING_WF_TIS}
+
+
+def ihist_mapping_workspace_bytes(mapping: int, h: int, w: int, nbins: int) -> int:
+    return int(load().ihist_mapping_workspace_bytes(mapping, h, w, nbins))
+
+
+def ihist_mapping_compute(mapping: int, h: int, w: int, nbins: int, d_in: int, in_pitch: int, d_out: int,
+                          d_work: int = 0, stream: int = 0) -> None:
+    """One of the paper's mappings (comparison kernels; see include/ihist.h)."""
+    _check(load().ihist_mapping_compute(mapping, h, w, nbins, d_in, in_pitch, d_out, d_work or None, stream),
+           "ihist_mapping_compute")
+
+
+def window_grid(h: int, w: int, win_h: int, win_w: int, stride: int):
+    """(ny, nx) of the window grid ihist_window_search scores."""
+    return (h - win_h) // stride + 1, (w - win_w) // stride + 1
 
 
 def ihist_sequence_host(plan: int, h_frames: int, frame_stride: int, nframes: int, d_slots: int,
@@ -422,6 +454,19 @@ class Plan:
         if out is None:
             out = torch.empty((n, self.nbins), dtype=torch.int32, device=rects.device)
         ihist_query(self.handle, hist.data_ptr(), rects.data_ptr(), n, out.data_ptr(), _stream(stream))
+        return out
+
+    def window_search(self, hist, target, win_h: int, win_w: int, stride: int, out=None, stream=None):
+        """Histogram-intersection score of every win_h x win_w window on a
+        stride grid against target (CUDA int32 [nbins]) -> int32 [ny][nx]."""
+        import torch
+        if target.dtype != torch.int32 or not target.is_contiguous() or target.numel() != self.nbins:
+            raise ValueError("target must be a contiguous int32 tensor of nbins counts")
+        ny, nx = window_grid(self.h, self.w, win_h, win_w, stride) if stride >= 1 else (0, 0)
+        if out is None:
+            out = torch.empty((max(ny, 0), max(nx, 0)), dtype=torch.int32, device=target.device)
+        ihist_window_search(self.handle, hist.data_ptr(), target.data_ptr(), win_h, win_w, stride, out.data_ptr(),
+                            _stream(stream))
         return out
 
     def status(self, stream=None) -> int:

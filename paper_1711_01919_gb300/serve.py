@@ -9,8 +9,9 @@ Requests arrive over time (Sec. 4.4's image sequences, served):
   recently used resident histograms that no pending query holds.
 * ``QueryRequest``  rectangles whose region histograms (Eq. 2) are wanted
   from a resident histogram.  The server picks the target among the
-  resident frames when the query is admitted (seeded, uniform) and holds it
-  until the query is answered; the rows are copied back to the host.
+  resident frames whose histogram is complete when the query is admitted
+  (seeded, uniform) and holds it until the query is answered; the rows are
+  copied back to the host.
 
 The loop is continuous batching, not a queue: every iteration it admits
 what has arrived and fits, puts all admitted frames that are not yet
@@ -21,9 +22,10 @@ compute.  Queries whose histogram is ready are launched as they come.
 Latency is taken from GPU event timestamps against a reference event
 recorded at the start, so it does not depend on how often the host polls.
 
-When only one frame is waiting, the batched server launches it alone
-(``ihist_compute`` with a per-shape plan): a one-frame batch only adds the
-descriptor upload.  Queries run on a stream of their own, so they do not
+When fewer than ``min_batch`` frames are waiting, the batched server
+launches them one by one (``ihist_compute`` with a per-shape plan): a short
+queue gains nothing from a shared launch, whose first frame would wait for
+the others.  Queries run on a stream of their own, so they do not
 queue behind frames that do not concern them.
 
 ``mode="plain"`` serves every frame with its own ``ihist_compute`` launch
@@ -36,6 +38,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import heapq
 import time
 
@@ -134,6 +137,10 @@ class HistStore:
     def resident(self):
         return list(self.entries.keys())
 
+    def ready_ids(self):
+        """Resident histograms whose computation has finished."""
+        return [rid for rid, e in self.entries.items() if e[2]]
+
     def payload(self, rid: int):
         return self.entries[rid][3]
 
@@ -173,19 +180,36 @@ class Server:
     """Continuous-batching request loop over an executor (see module doc)."""
 
     def __init__(self, executor, budget_bytes: int, max_batch: int = 64, mode: str = "batched",
-                 seed: int = 4):
+                 seed: int = 4, min_batch: int = 4, keep_results: bool = True):
         self.ex = executor
         self.store = HistStore(budget_bytes)
         self.max_batch = max_batch if mode == "batched" else 1
+        # fewer waiting frames than this go out one launch each: a short
+        # queue gains nothing from a shared launch, and the first frame of a
+        # batch would wait for the others
+        self.min_batch = min_batch if mode == "batched" else 1
         self.mode = mode
         self.rng = np.random.default_rng(seed)
         self.done = []
         self.results = {}
+        self.keep_results = keep_results  # copy each query's rows out of the executor's reusable buffers
         self.batch_sizes = collections.Counter()
+        self.host_ms = {"frames": [], "query": []}  # host time spent issuing each launch
 
     def run(self, requests, clock, max_wall: float = 600.0):
         """Serve `requests` (sorted by t_arrival).  clock() returns seconds since
-        the start; the loop ends when every request has completed."""
+        the start; the loop ends when every request has completed.  Python's
+        cyclic garbage collector is paused meanwhile: its full passes over the
+        request objects take milliseconds and would show as latency."""
+        was_enabled = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(requests, clock, max_wall)
+        finally:
+            if was_enabled:
+                gc.enable()
+
+    def _run(self, requests, clock, max_wall):
         pending = collections.deque(requests)
         admit_frames = collections.deque()   # arrived, waiting for budget
         ready_frames = []                    # admitted, not launched
@@ -204,7 +228,7 @@ class Server:
                     admit_frames.append(r)
                     arrived_frames[r.rid] = r
                 else:
-                    live = self.store.resident()
+                    live = self.store.ready_ids()
                     if not live:
                         self.done.append(Done(r.rid, "query", r.t_arrival, t, "rejected"))
                         continue
@@ -227,21 +251,25 @@ class Server:
             for _ in range(len(waiting_queries)):
                 q = waiting_queries.popleft()
                 if self.store.ready(q.target):
+                    t_call = clock()
                     h = self.ex.launch_query(q, self.store.payload(q.target), t)
                     h["t_launch"] = clock()
+                    self.host_ms["query"].append(1e3 * (h["t_launch"] - t_call))
                     inflight.append((h, "query", q))
                 else:
                     waiting_queries.append(q)
             # 4. one batched launch of everything admitted (continuous batching)
             while ready_frames:
-                batch, ready_frames = ready_frames[:self.max_batch], ready_frames[self.max_batch:]
+                take = self.max_batch if len(ready_frames) >= self.min_batch else 1
+                batch, ready_frames = ready_frames[:take], ready_frames[take:]
+                t_call = clock()
                 h = self.ex.launch_frames(batch, t)
                 h["t_launch"] = clock()
+                self.host_ms["frames"].append(1e3 * (h["t_launch"] - t_call))
                 self.batch_sizes[len(batch)] += 1
                 inflight.append((h, "frames", batch))
-                if self.mode != "batched":
-                    continue
-                break
+                if len(batch) > 1:
+                    break  # one shared launch per iteration; later arrivals join the next
             # 5. completions
             still = []
             for h, kind, obj in inflight:
@@ -255,7 +283,9 @@ class Server:
                     else:
                         self.store.unpin(obj.target)
                         self.store.touch(obj.target)
-                        self.results[obj.rid] = h.get("result")
+                        if self.keep_results:
+                            r = h.get("result")
+                            self.results[obj.rid] = r.clone() if hasattr(r, "clone") else r
                         self.done.append(Done(obj.rid, "query", obj.t_arrival, td, target=obj.target,
                                               t_launch=h["t_launch"]))
                 else:
@@ -265,7 +295,8 @@ class Server:
 
     def report(self, wall_s: float):
         out = {"mode": self.mode, "evicted": self.store.evicted,
-               "launch_sizes": {str(k): v for k, v in sorted(self.batch_sizes.items())}}
+               "launch_sizes": {str(k): v for k, v in sorted(self.batch_sizes.items())},
+               "host_issue_p50_ms": {k: float(np.percentile(v, 50)) if v else None for k, v in self.host_ms.items()}}
         for kind in ("frame", "query"):
             ok = [d for d in self.done if d.kind == kind and d.status == "ok"]
             lat = np.array([d.t_done - d.t_arrival for d in ok]) * 1e3
@@ -326,7 +357,7 @@ class GpuExecutor:
     are returned to it on eviction.
     """
 
-    def __init__(self, mode="batched", nslots=64, max_shape=(1080, 1920, 64), query_slots=64):
+    def __init__(self, mode="batched", nslots=64, max_shape=(1080, 1920, 64), query_slots=8, max_rects=10000):
         import torch
 
         from . import ihist
@@ -356,13 +387,46 @@ class GpuExecutor:
             e.record(self.stream)
         self.t0_event = torch.cuda.Event(enable_timing=True)
         self.t0_wall = 0.0
-        self.query_bufs = []
+        # query slots, reused round robin: pinned and device buffers for the
+        # rectangles and the rows, so that issuing a query allocates nothing
+        self.max_rects = max_rects
+        self.qslots = []
+        for _ in range(query_slots):
+            self.qslots.append({
+                "h_rects": torch.empty((max_rects, 4), dtype=torch.int32, pin_memory=True),
+                "d_rects": torch.empty((max_rects, 4), dtype=torch.int32, device="cuda"),
+                "d_out": torch.empty((max_rects * 256,), dtype=torch.int32, device="cuda"),
+                "h_out": torch.empty((max_rects * 256,), dtype=torch.int32, pin_memory=True),
+                "free": None,  # event: the slot's last rows have reached the host
+            })
+        self.next_qslot = 0
 
     def warm(self, shapes):
-        """Create the per-shape plans before serving: plan creation allocates
-        and synchronises the device, which must not happen inside the loop."""
+        """Create the per-shape plans and run every kernel once before
+        serving: plan creation allocates and synchronises the device, and a
+        kernel's first launch loads its code, neither of which may happen
+        inside the timed loop."""
+        torch = self.torch
+        shapes = list(shapes)
         for (h, w, b) in shapes:
-            self._plan(h, w, b)
+            p = self._plan(h, w, b)
+            out = torch.empty((b, h, w), dtype=torch.int32, device="cuda")
+            p.compute(torch.zeros((h, w), dtype=torch.uint8, device="cuda"), out, stream=self.s)
+            p.query(out, torch.zeros((1, 4), dtype=torch.int32, device="cuda"), stream=self.s)
+        if self.mode == "batched" and shapes:
+            for batch, ins in zip(self.batches, self.inputs[1:]):
+                sel = shapes[:min(len(shapes), len(ins))]
+                views = [ins[i].view(-1)[:h * w].view(h, w) for i, (h, w, b) in enumerate(sel)]
+                outs = [torch.empty((b, h, w), dtype=torch.int32, device="cuda") for (h, w, b) in sel]
+                batch.set_io(views, outs, nbins=[b for (h, w, b) in sel], layouts=[0] * len(sel), stream=self.s)
+                batch.compute(stream=self.s)
+        torch.cuda.synchronize()
+        for p in self.plans.values():
+            if p.status() != self.ih.IHIST_OK:
+                raise RuntimeError("device status error while warming up")
+        for batch in self.batches:
+            if batch.status() != self.ih.IHIST_OK:
+                raise RuntimeError("device status error while warming up a batch")
 
     def start(self):
         self.torch.cuda.synchronize()
@@ -411,20 +475,27 @@ class GpuExecutor:
     def launch_query(self, q, payload, t):
         # the server launches a query only once its histogram is complete,
         # and keeps the histogram resident until the query is done
-        torch = self.torch
+        torch, ih = self.torch, self.ih
         hist, h, w, b = payload
-        rects = torch.from_numpy(np.ascontiguousarray(q.rects, dtype=np.int32)).pin_memory()
+        n = len(q.rects)
+        if n > self.max_rects:
+            raise ValueError("query of %d rectangles exceeds the executor's %d" % (n, self.max_rects))
+        slot = self.qslots[self.next_qslot]
+        self.next_qslot = (self.next_qslot + 1) % len(self.qslots)
+        if slot["free"] is not None:
+            slot["free"].synchronize()  # the slot's previous rows are on the host (rarely waits)
+        slot["h_rects"].numpy()[:n] = q.rects
+        qs = self.qstream.cuda_stream
+        d_rects, d_out, h_out = slot["d_rects"], slot["d_out"], slot["h_out"]
         with torch.cuda.stream(self.qstream):
-            d_rects = torch.empty(rects.shape, dtype=torch.int32, device="cuda")
-            d_rects.copy_(rects, non_blocking=True)
-            out = torch.empty((rects.shape[0], b), dtype=torch.int32, device="cuda")
-            self._plan(h, w, b).query(hist, d_rects, out, stream=self.qstream.cuda_stream)
-            host = torch.empty(out.shape, dtype=torch.int32).pin_memory()
-            host.copy_(out, non_blocking=True)
+            d_rects[:n].copy_(slot["h_rects"][:n], non_blocking=True)
+            ih.ihist_query(self._plan(h, w, b).handle, hist.data_ptr(), d_rects.data_ptr(), n, d_out.data_ptr(), qs)
+            h_out[:n * b].copy_(d_out[:n * b], non_blocking=True)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(self.qstream)
+        slot["free"] = ev
         hist.record_stream(self.qstream)
-        return {"ev": ev, "result": host, "keep": (rects, d_rects, out)}
+        return {"ev": ev, "result": h_out[:n * b].view(n, b)}
 
     def poll(self, handle, t):
         return handle["ev"].query()
@@ -456,9 +527,9 @@ def serve(mode="batched", duration_s=2.0, budget_gb=40.0, seed=None, frame_rate=
         # the same requests, arriving 1000 times faster than the server can take them
         for r in reqs:
             r.t_arrival *= 1e-3
-    ex = GpuExecutor(mode)
+    ex = GpuExecutor(mode, max_rects=max(1, rects_per_query))
     ex.warm(sorted({(r.h, r.w, r.nbins) for r in reqs if isinstance(r, FrameRequest)}))
-    srv = Server(ex, int(budget_gb * (1 << 30)), mode=mode)
+    srv = Server(ex, int(budget_gb * (1 << 30)), mode=mode, keep_results=False)
     ex.start()
     t0 = time.perf_counter()
     srv.run(reqs, ex.clock)

@@ -98,3 +98,18 @@ def test_other_bin_structures_reject_bad_arguments_before_touching_cuda(lib):
             make()
         assert e.value.code == code
     assert ihist.ihist_plan_channels(None) == 0
+
+
+def test_window_search_rejects_null_plan(lib):
+    assert lib.ihist_window_search(None, None, None, 1, 1, 1, None, None) == ihist.IHIST_ERR_INVALID_ARG
+    assert ihist.window_grid(1080, 1920, 64, 64, 4) == (255, 465)
+    assert ihist.window_grid(10, 10, 10, 10, 3) == (1, 1)
+
+
+def test_mapping_arguments_checked_before_touching_cuda(lib):
+    assert ihist.ihist_mapping_workspace_bytes(ihist.IHIST_MAPPING_CW_STS, 1080, 1920, 64) == 530841600
+    assert ihist.ihist_mapping_workspace_bytes(ihist.IHIST_MAPPING_WF_TIS, 1080, 1920, 64) == 0
+    for mapping, h, w, b in [(0, 8, 8, 4), (4, 8, 8, 4), (2, 0, 8, 4), (3, 8, 8, 0), (1, 8, 8, 4)]:
+        # (the last: CW-STS without its workspace)
+        assert lib.ihist_mapping_compute(mapping, h, w, b, ctypes.c_void_p(16), w, ctypes.c_void_p(16), None,
+                                         None) == ihist.IHIST_ERR_INVALID_ARG

@@ -28,6 +28,7 @@ def run_server(mode, duration=0.04, budget_gb=40.0, saturate=False):
         for r in reqs:
             r.t_arrival = 0.0
     ex = serve.GpuExecutor(mode, nslots=16)
+    ex.warm(sorted({(r.h, r.w, r.nbins) for r in reqs if isinstance(r, serve.FrameRequest)}))
     srv = serve.Server(ex, int(budget_gb * (1 << 30)), max_batch=16, mode=mode)
     ex.start()
     srv.run(reqs, ex.clock)
@@ -65,8 +66,11 @@ def check_alone(srv, reqs):
 def test_served_results_equal_alone(mode):
     srv, ex, reqs = run_server(mode)
     done = srv.done
-    assert all(d.status == "ok" for d in done)
     assert len(done) == len(reqs)
+    assert all(d.status == "ok" for d in done if d.kind == "frame")
+    # a query is refused only if it came before any histogram was complete
+    first_ready = min(d.t_done for d in done if d.kind == "frame")
+    assert all(d.status == "ok" or d.t_arrival < first_ready for d in done if d.kind == "query")
     nq = check_alone(srv, reqs)
     assert nq >= 3
     ex.close()

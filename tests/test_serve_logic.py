@@ -90,3 +90,27 @@ def test_report_percentiles():
     rep = srv.report(1.0)
     assert rep["frame"]["completed"] == 20
     assert rep["frame"]["p50_ms"] <= rep["frame"]["p99_ms"] <= rep["frame"]["max_ms"]
+
+
+def test_short_queues_launch_frames_one_by_one():
+    ex = serve.FakeExecutor(frame_latency=1e-3)
+    srv = serve.Server(ex, budget_bytes=1 << 30, min_batch=4)
+    srv.run(frames(3), Clock())
+    assert [l[1] for l in ex.launches] == [[0], [1], [2]]
+    ex = serve.FakeExecutor(frame_latency=1e-3)
+    srv = serve.Server(ex, budget_bytes=1 << 30, min_batch=4)
+    srv.run(frames(4), Clock())
+    assert [l[1] for l in ex.launches] == [[0, 1, 2, 3]]
+    assert srv.report(1.0)["launch_sizes"] == {"4": 1}
+
+
+def test_query_targets_only_finished_histograms():
+    # frame 0 is still computing when the query arrives: no target yet -> rejected;
+    # frame 1 finished before the second query -> that one is served on it
+    ex = serve.FakeExecutor(frame_latency=5e-3)
+    srv = serve.Server(ex, budget_bytes=1 << 30, seed=1)
+    reqs = [serve.FrameRequest(0, 0.0, 10, 10, 4), serve.QueryRequest(10, 1e-3, np.zeros((1, 4), np.int32)),
+            serve.QueryRequest(11, 2e-2, np.zeros((1, 4), np.int32))]
+    done = {d.rid: d for d in srv.run(reqs, Clock(1e-4))}
+    assert done[10].status == "rejected"
+    assert done[11].status == "ok" and done[11].target == 0
