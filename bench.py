@@ -66,6 +66,22 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(values, world: int, device=None) -> list:
+    """Element-wise maximum of per-rank timings over all ranks: the slowest
+    replica decides the job's time."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(frames_per_rank: int, steps: int, world: int, elapsed_ms: float) -> float:
+    """Frames per second of the whole job: every rank's frames over the slowest rank's time."""
+    return world * frames_per_rank * steps / (elapsed_ms / 1000.0)
+
+
 def make_frames(rank: int, n: int = 0) -> np.ndarray:
     from paper_1711_01919_gb300 import synth
     n = n or NFRAMES
@@ -374,6 +390,11 @@ def mappings_report(stream, peak: float) -> dict:
     with ihist.Plan(H, W, NBINS) as plan:
         ms = _median_ms(lambda: ihist.ihist_compute(plan.handle, img.data_ptr(), W, out.data_ptr(), s), stream)
     rep["fused_look_back"] = {"ms_per_frame": ms, "frames_per_s": 1e3 / ms, "frac": byts / ms / 1e6 / peak}
+    # the same frame into the pixel-major layout [y][x][b]
+    with ihist.Plan(H, W, NBINS, ihist.IHIST_PIXEL_MAJOR) as plan:
+        ms = _median_ms(lambda: ihist.ihist_compute(plan.handle, img.data_ptr(), W, out.data_ptr(), s), stream)
+        rep["fused_look_back_pixel_major"] = {"ms_per_frame": ms, "frames_per_s": 1e3 / ms,
+                                              "frac": byts / ms / 1e6 / peak, "tile": plan.tune}
     return rep
 
 
@@ -638,14 +659,10 @@ def main():
     write_probe_gbs = 10 * probe.numel() * 4 / (w_start.elapsed_time(w_end) / 1000.0) / 1e9
     del probe
 
-    times = torch.tensor([elapsed_ms, e2e_ms, plain_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    elapsed_ms, e2e_ms, plain_ms = times.tolist()
+    elapsed_ms, e2e_ms, plain_ms = max_over_ranks([elapsed_ms, e2e_ms, plain_ms], world, dev)
 
     if rank == 0:
-        frames_total = world * NFRAMES * args.steps
-        value = frames_total / (elapsed_ms / 1000.0)
+        value = job_throughput(NFRAMES, args.steps, world, elapsed_ms)
         peak, peak_kind = measured_peak()
         bytes_per_launch = NFRAMES * algorithmic_bytes_per_frame()
         mean_kernel_s = statistics.fmean(kernel_ms) / 1000.0
@@ -664,7 +681,7 @@ def main():
                 "batch_items_per_launch": batch.items(),
                 "scan_launch_ms_median": statistics.median(kernel_ms),
                 "plain_per_frame": {
-                    "value": world * NFRAMES * pf_steps / (plain_ms / 1000.0), "unit": "frames/s",
+                    "value": job_throughput(NFRAMES, pf_steps, world, plain_ms), "unit": "frames/s",
                     "steps": pf_steps, "form": "%d x (ihist_compute + ihist_query) per step" % NFRAMES,
                     "tile": plan.tune},
             },
@@ -675,7 +692,7 @@ def main():
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
                          "write_probe_gbs": write_probe_gbs,
                          "frac_of_write_probe": achieved / write_probe_gbs},
-            "e2e": {"value": world * NFRAMES * e2e_steps / (e2e_ms / 1000.0), "unit": "frames/s",
+            "e2e": {"value": job_throughput(NFRAMES, e2e_steps, world, e2e_ms), "unit": "frames/s",
                     "h2d_bytes_per_step": NFRAMES * H * W, "d2h_bytes_per_step": NFRAMES * NRECTS * NBINS * 4,
                     "steps": e2e_steps,
                     "api": "ihist_batch_upload_compute on two alternating %d-frame batches (pinned host frames, "
