@@ -261,17 +261,24 @@ typedef struct {
 
 /* Plan a batch of n >= 1 frames (limits per frame as for ihist_plan); the
  * frames also fix the capacity of the batch's n slots (see
- * ihist_batch_set_io).  tune may be NULL; its bins_per_cta (4 or 8),
- * rows_per_band and warps_per_cta apply to every frame; chunks per warp and
- * groups per CTA are chosen per frame to fill the CTA's warps.  Frames wider
- * than 4 x warps_per_cta chunks of 128 columns give IHIST_ERR_UNSUPPORTED
- * (at most 8192 columns with 16 warps).  Frames bound
+ * ihist_batch_set_io).  tune may be NULL; its bins_per_cta (4, 8 or 16;
+ * default 4, or 16 / 8 when a frame is pixel-major), rows_per_band and
+ * warps_per_cta apply to every frame; chunks per warp and groups per CTA
+ * are chosen per frame to fill the CTA's warps.  Frames wider than
+ * 4 x warps_per_cta chunks of 128 columns (2 x with 16 bins per CTA) give
+ * IHIST_ERR_UNSUPPORTED (at most 8192 columns with 16 warps).  Frames bound
  * later by ihist_batch_set_io keep within the launch shape the planned
  * frames fixed (chunks per warp, carry width per CTA), which may leave some
  * of a narrower frame's CTA idle.  Allocates the batch's device workspace
  * and pinned staging buffers. */
 int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_tune_t *tune,
                      ihist_batch_t *out);
+
+/* The launch shape a batch resolved to: rows_per_band (the requested band
+ * height; short frames use fewer rows), bins_per_cta, chunks_per_warp (the
+ * largest any frame may use), ctas_per_sm, timeout_us, warps_per_cta;
+ * groups_per_cta is 0 (chosen per frame). */
+int ihist_batch_get_tune(ihist_batch_t batch, ihist_tune_t *out);
 
 /* Bind the batch to n frames (1 <= n <= the planned count), for example a
  * new set of requests.  Frame i takes slot i, whose carry workspace was

@@ -150,7 +150,7 @@ static int occupancy(ScanFn fn, int threads, size_t smem) {
 // bytes) x (warps per SM, up to 24) x (fraction of CTA bin groups in use).
 // Fields the caller fixed (non-zero) are kept.
 static void default_tiling(int h, int ngroups, int wpg, int G, int nchunks, int sms, ScanFn fn,
-                           size_t optin, int *R, int *gpc) {
+                           size_t optin, int layout, int *R, int *gpc) {
   double best = -1.0;
   int best_r = *R ? *R : std::min(h, 8), best_g = *gpc ? *gpc : 1;
   const int g_lo = *gpc ? *gpc : 1;
@@ -161,7 +161,7 @@ static void default_tiling(int h, int ngroups, int wpg, int G, int nchunks, int 
     const double used = (double)ngroups / (double)(ngsets * gp);
     const int r_lo = *R ? *R : std::min(h, 8), r_hi = *R ? *R : std::min(h, 255);
     for (int r = r_lo; r <= r_hi; ++r) {
-      const size_t smem = smem_layout(NW, r, G, nchunks * gp).bytes;
+      const size_t smem = smem_layout(NW, r, G, nchunks * gp, pm_staged(layout, G)).bytes;
       if (smem > optin) break;
       const int occ = occupancy(fn, NW * 32, smem);
       if (occ < 1) break;
@@ -211,16 +211,15 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
     return IHIST_ERR_CUDA;
   const int nchunks = (w + kChunk - 1) / kChunk;
   // Pixel-major output: a pixel's counts of one bin group are G contiguous
-  // words and the groups of a pixel belong to different CTAs, so each warp
-  // store touches one 16-byte piece of 32 pixels' records; larger groups
-  // make those pieces longer (measured on 1080p x 64: G = 4 762 us, G = 8
-  // 415 us, G = 16 with two chunks per warp 300 us per frame).
+  // words and the groups of a pixel belong to different CTAs, so larger
+  // groups give longer contiguous pieces per pixel record; rows are staged
+  // in shared memory so that a warp store writes whole pieces (measured on
+  // 1080p x 64 per frame: G = 4 unstaged 762 us; G = 16 unstaged 325 us,
+  // staged 159 us).
   const bool pm_wide = layout == IHIST_PIXEL_MAJOR && nbins >= 16 && nchunks <= 32 && !table;
   if (t.bins_per_cta == 0) t.bins_per_cta = layout == IHIST_PIXEL_MAJOR ? (pm_wide ? 16 : 8) : 4;
-  if (t.chunks_per_warp == 0) {
+  if (t.chunks_per_warp == 0)
     t.chunks_per_warp = nchunks <= 16 ? 1 : nchunks <= 32 ? 2 : nchunks <= 64 ? 4 : 8;
-    if (t.bins_per_cta == 16 && layout == IHIST_PIXEL_MAJOR && nchunks > 8) t.chunks_per_warp = 2;
-  }
   if (t.timeout_us == 0) t.timeout_us = kDefaultTimeoutUs;
   const int wpg = (nchunks + t.chunks_per_warp - 1) / t.chunks_per_warp;
   const int mmax = mmax_for(t.chunks_per_warp);
@@ -233,7 +232,7 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   const int ngroups = (nbins + t.bins_per_cta - 1) / t.bins_per_cta;
   if (t.groups_per_cta > ngroups) t.groups_per_cta = ngroups;
   if (t.rows_per_band == 0 || t.groups_per_cta == 0)
-    default_tiling(h, ngroups, wpg, t.bins_per_cta, nchunks, sms, fn, optin, &t.rows_per_band,
+    default_tiling(h, ngroups, wpg, t.bins_per_cta, nchunks, sms, fn, optin, layout, &t.rows_per_band,
                    &t.groups_per_cta);
 
   ihist_plan_s *p = new (std::nothrow) ihist_plan_s;
@@ -260,7 +259,7 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   p->nitems = (unsigned int)p->nbands * (unsigned int)p->ngsets;
   p->timeout_us = t.timeout_us;
   p->fault_skip_band = t.fault_skip_band;
-  p->smem_bytes = smem_layout(p->NW, p->R, p->G, p->nchunks * p->gpc).bytes;
+  p->smem_bytes = smem_layout(p->NW, p->R, p->G, p->nchunks * p->gpc, pm_staged(layout, p->G)).bytes;
   const int occ = p->smem_bytes <= optin ? occupancy(fn, p->NW * 32, p->smem_bytes) : 0;
   if (occ < 1) {
     delete p;
@@ -704,7 +703,7 @@ bool frame_vec_ok(const ihist_frame_t &fr) {
 }  // namespace
 
 struct ihist_batch_s {
-  int device, sms, cap, n, G, warps, mmax, R_req, R_max, ncg_max, ctas_cap;
+  int device, sms, cap, n, G, warps, mmax, R_req, R_max, ncg_max, ctas_cap, stage;
   int ctas_per_sm[2][2];  // occupancy of each (tma, vec) variant
   bool tma, vec;          // variant the current frames allow
   unsigned int timeout_us, total;
@@ -835,13 +834,17 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   std::memset(&t, 0, sizeof(t));
   if (tune) t = *tune;
   if (t.bins_per_cta == 0) {
-    // 8-bin groups when any frame is pixel-major (longer contiguous pieces
-    // per pixel record: 20.9 ms against 68.7 ms for 64 pixel-major 1080p frames)
-    t.bins_per_cta = 4;
-    for (int i = 0; i < n; ++i)
-      if (frames[i].layout == IHIST_PIXEL_MAJOR) t.bins_per_cta = 8;
+    // larger bin groups when any frame is pixel-major (longer contiguous
+    // pieces per pixel record): 16 when every frame has at least 16 bins and
+    // fits 16 warps x 2 chunks, else 8
+    bool pm = false, wide16 = true;
+    for (int i = 0; i < n; ++i) {
+      pm = pm || frames[i].layout == IHIST_PIXEL_MAJOR;
+      wide16 = wide16 && frames[i].nbins >= 16 && frames[i].w <= kBatchWarps * 2 * kChunk;
+    }
+    t.bins_per_cta = pm ? (wide16 ? 16 : 8) : 4;
   }
-  if (t.bins_per_cta != 4 && t.bins_per_cta != 8) return IHIST_ERR_INVALID_ARG;
+  if (t.bins_per_cta != 4 && t.bins_per_cta != 8 && t.bins_per_cta != 16) return IHIST_ERR_INVALID_ARG;
   if (t.rows_per_band < 0 || t.rows_per_band > 255) return IHIST_ERR_INVALID_ARG;
   if (t.ctas_per_sm < 0 || t.ctas_per_sm > 32) return IHIST_ERR_INVALID_ARG;
   if (t.warps_per_cta != 0 && t.warps_per_cta != 4 && t.warps_per_cta != 8 && t.warps_per_cta != 16)
@@ -862,18 +865,25 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   b->sms = sms;
   b->cap = n;
   b->G = t.bins_per_cta;
+  // pixel-major frames stage their rows in shared memory
+  b->stage = 0;
+  for (int i = 0; i < n; ++i)
+    if (pm_staged(frames[i].layout, b->G)) b->stage = 1;
   // default: 8-warp CTAs (4 per SM overlap their count, look-back and emit
   // phases better than 2 of 16 warps: measured 5% faster on 1080p frames)
   // when every frame fits 8 warps x 4 chunks, else 16 warps
   b->warps = t.warps_per_cta;
   if (b->warps == 0) {
-    b->warps = 8;
+    // 16-warp CTAs for pixel-major batches (staged rows: 10.5 against 11.7 ms
+    // for 64 pixel-major 1080p frames)
+    b->warps = b->stage ? kBatchWarps : 8;
     for (int i = 0; i < n; ++i)
       if (frames[i].w > 8 * 4 * kChunk) b->warps = kBatchWarps;
   }
   b->timeout_us = t.timeout_us ? t.timeout_us : kDefaultTimeoutUs;
+  const int max_m = b->G == 16 ? 2 : 4;  // chunks per warp the instantiations cover
   // every kernel variant the batch may launch may use the opt-in shared memory
-  for (int mm = 1; mm <= 4; mm <<= 1)
+  for (int mm = 1; mm <= max_m; mm <<= 1)
     for (int tma = 0; tma < 2; ++tma)
       for (int vec = 0; vec < 2; ++vec) {
         BatchFn fn = batch_fn(b->G, mm, tma != 0, vec != 0);
@@ -896,33 +906,40 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   // every frame must have a tiling in CTAs of this many warps
   for (int i = 0; i < n; ++i) {
     FrameDesc f;
-    if (!batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, 8, 4, INT_MAX,
-                            b->warps, &f)) {
+    if (!batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, 8, max_m,
+                            INT_MAX, b->warps, &f)) {
       delete b;
       return IHIST_ERR_UNSUPPORTED;
     }
   }
   b->R_req = t.rows_per_band;
   if (b->R_req == 0) {
-    b->R_req = 8;
-    for (int r = 64; r >= 8; --r) {
+    // the largest R (at most 64) that keeps the CTAs per SM that the
+    // smallest bands allow (registers permitting: 4 of 8 warps or 2 of 16
+    // warps with 4 or 8 bins per CTA, 1 with 16)
+    auto occ_at = [&](int r) {
       int rmax = 1, ncg = 1, mm = 1;
       for (int i = 0; i < n; ++i) {
         FrameDesc f;
-        batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, r, 4, INT_MAX,
+        batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, r, max_m, INT_MAX,
                            b->warps, &f);
         rmax = std::max(rmax, f.R);
         ncg = std::max(ncg, f.nchunks * f.gpc);
         mm = std::max(mm, f.m);
       }
       int occ = 0;
-      const size_t smem = smem_layout(b->warps, rmax, b->G, ncg).bytes;
+      const size_t smem = smem_layout(b->warps, rmax, b->G, ncg, b->stage != 0).bytes;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_fn(b->G, mmax_for(mm), true, true),
                                                         b->warps * 32, smem) != cudaSuccess) {
         cudaGetLastError();
         occ = 0;
       }
-      if (occ * b->warps >= 32) {
+      return occ;
+    };
+    const int target = std::max(1, occ_at(8));
+    b->R_req = 8;
+    for (int r = 64; r >= 8; --r) {
+      if (occ_at(r) >= target) {
         b->R_req = r;
         break;
       }
@@ -933,7 +950,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   int mm = 1;
   size_t nci_total = 0;
   for (int i = 0; i < n; ++i) {
-    batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, b->R_req, 4,
+    batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, b->R_req, max_m,
                        INT_MAX, b->warps, &plan_fd[i]);
     mm = std::max(mm, plan_fd[i].m);
     b->R_max = std::max(b->R_max, plan_fd[i].R);
@@ -942,7 +959,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
     nci_total += frame_nci(plan_fd[i]);
   }
   b->mmax = mmax_for(mm);
-  b->smem_bytes = smem_layout(b->warps, b->R_max, b->G, b->ncg_max).bytes;
+  b->smem_bytes = smem_layout(b->warps, b->R_max, b->G, b->ncg_max, b->stage != 0).bytes;
   for (int tma = 0; tma < 2; ++tma)
     for (int vec = 0; vec < 2; ++vec) {
       BatchFn fn = batch_fn(b->G, b->mmax, tma != 0, vec != 0);
@@ -1043,6 +1060,20 @@ static int check_batch_device(const ihist_batch_s *b) {
   return dev == b->device ? IHIST_OK : IHIST_ERR_INVALID_ARG;
 }
 
+extern "C" int ihist_batch_get_tune(ihist_batch_t b, ihist_tune_t *out) {
+  if (!b || !out) return IHIST_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->rows_per_band = b->R_req;
+  out->bins_per_cta = b->G;
+  out->chunks_per_warp = b->mmax;
+  out->ctas_per_sm = b->ctas_per_sm[1][1];
+  out->timeout_us = b->timeout_us;
+  out->fault_skip_band = -1;
+  out->groups_per_cta = 0;  // chosen per frame
+  out->warps_per_cta = b->warps;
+  return IHIST_OK;
+}
+
 extern "C" int ihist_batch_set_io(ihist_batch_t b, const ihist_frame_t *frames, int n, void *stream) {
   if (!b || !frames) return IHIST_ERR_INVALID_ARG;
   int rc = check_batch_device(b);
@@ -1063,7 +1094,7 @@ extern "C" int ihist_batch_compute(ihist_batch_t b, void *stream) {
   const unsigned int grid = std::min<unsigned int>(b->total, (unsigned int)(cps * b->sms));
   const unsigned long long timeout_ns = (unsigned long long)b->timeout_us * 1000ull;
   fn<<<grid, b->warps * 32, b->smem_bytes, (cudaStream_t)stream>>>(
-      b->d_fd, b->d_tm, b->d_end, b->n, b->R_max, b->ncg_max, b->ctrl, timeout_ns);
+      b->d_fd, b->d_tm, b->d_end, b->n, b->R_max, b->ncg_max, b->stage, b->ctrl, timeout_ns);
   if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
   if (cudaEventRecord(b->computed, (cudaStream_t)stream) != cudaSuccess) return IHIST_ERR_CUDA;
   b->launched = true;

@@ -10,7 +10,7 @@
 namespace ihist {
 
 using ScanFn = void (*)(FrameDesc, const CUtensorMap, Ctrl *, unsigned long long);
-using BatchFn = void (*)(const FrameDesc *, const CUtensorMap *, const unsigned int *, int, int, int,
+using BatchFn = void (*)(const FrameDesc *, const CUtensorMap *, const unsigned int *, int, int, int, int,
                          Ctrl *, unsigned long long);
 
 // Kernel for (G, MMAX = chunks-per-warp bound, TMA input staging, 16-byte
@@ -22,6 +22,7 @@ ScanFn scan_fn_lut_g4(int mmax, bool tma, bool vec);  // binning through a value
 ScanFn scan_fn_lut_g8(int mmax, bool tma, bool vec);
 BatchFn batch_fn_g4(int mmax, bool tma, bool vec);
 BatchFn batch_fn_g8(int mmax, bool tma, bool vec);
+BatchFn batch_fn_g16(int mmax, bool tma, bool vec);  // mmax <= 2
 
 inline ScanFn scan_fn(int G, int mmax, bool tma, bool vec, bool lut = false) {
   if (lut) return G == 4 ? scan_fn_lut_g4(mmax, tma, vec) : G == 8 ? scan_fn_lut_g8(mmax, tma, vec) : nullptr;
@@ -37,6 +38,7 @@ inline BatchFn batch_fn(int G, int mmax, bool tma, bool vec) {
   switch (G) {
     case 4: return batch_fn_g4(mmax, tma, vec);
     case 8: return batch_fn_g8(mmax, tma, vec);
+    case 16: return batch_fn_g16(mmax, tma, vec);
     default: return nullptr;
   }
 }

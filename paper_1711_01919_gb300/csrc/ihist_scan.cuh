@@ -64,10 +64,14 @@ struct FrameDesc {
 
 // Dynamic shared memory of one CTA, carved from a 128-byte aligned base.
 struct SmemLayout {
-  uint32_t tile_off, row_off, ctot_off, bar_off, bytes;
+  uint32_t tile_off, row_off, ctot_off, bar_off, stage_off, bytes;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int NW, int R, int G, int nchunks) {
+// Pixel-major rows go through a per-warp staging area when a bin group has
+// at least 8 bins (see emit_pixel_major_staged).
+__host__ __device__ inline bool pm_staged(int layout, int G) { return layout == 1 && G >= 8; }
+
+__host__ __device__ inline SmemLayout smem_layout(int NW, int R, int G, int nchunks, bool stage = false) {
   SmemLayout L;
   uint32_t off = 0;
   L.tile_off = off;  // [NW][R][128] bytes
@@ -80,6 +84,9 @@ __host__ __device__ inline SmemLayout smem_layout(int NW, int R, int G, int nchu
   off = (off + 7u) & ~7u;
   L.bar_off = off;  // [NW] mbarriers
   off += (uint32_t)NW * 8u;
+  off = (off + 15u) & ~15u;
+  L.stage_off = off;  // [NW][128 px][G] u32 staging of pixel-major rows
+  if (stage) off += (uint32_t)NW * kChunk * (uint32_t)G * 4u;
   L.bytes = off + 128u;  // + base alignment slack
   return L;
 }
@@ -167,12 +174,61 @@ __device__ __forceinline__ bool stage_tile(const FrameDesc &f, const CUtensorMap
 
 // ---------------------------------------------------------------------------
 // One work item: band k, bin group g.
+// Slot of pixel p's quad r (4 bins) in a warp's staging area of
+// [G/4 quads][128 pixels] 16-byte slots.  The XOR swizzle makes both the
+// writes (lane -> its 4 pixels) and the reads (G/4 lanes per pixel) hit 8
+// distinct 16-byte bank groups per quarter warp.
+template <int GQ>
+__device__ __forceinline__ int stage_slot(int r, int p) {
+  constexpr int kShift = GQ >= 4 ? 1 : GQ == 2 ? 2 : 3;
+  return r * kChunk + (p & ~7) + ((p ^ ((p >> 3) & 3) ^ (r << kShift)) & 7);
+}
+
+// Pixel-major store of one row of a warp's 128-pixel chunk through shared
+// memory.  A pixel's record is B words; this CTA owns G of them.  Stored
+// straight from registers, each warp store would put 16 bytes into each of
+// 32 pixels' records; staged, G/4 consecutive lanes write one pixel's G
+// contiguous words, so a warp store covers 32/(G/4) records in full pieces.
+template <int G, bool VEC>
+__device__ __forceinline__ void emit_pixel_major_staged(const FrameDesc &f, uint4 *stage, const uint32_t (&acc)[G][4],
+                                                        int lane, int cbase, int y, int g) {
+  constexpr int GQ = G / 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int r = 0; r < GQ; ++r)
+      stage[stage_slot<GQ>(r, 4 * lane + i)] =
+          make_uint4(acc[4 * r][i], acc[4 * r + 1][i], acc[4 * r + 2][i], acc[4 * r + 3][i]);
+  __syncwarp();
+  constexpr int PPI = 32 / GQ;  // pixels per warp store
+  const int k = lane / GQ, r = lane % GQ;
+  const bool full = VEC && (f.B & 3) == 0 && g * G + 4 * r + 4 <= f.B;
+#pragma unroll 4
+  for (int s = 0; s < kChunk / PPI; ++s) {
+    const int p = s * PPI + k;
+    const int x = cbase + p;
+    if (x < f.W) {
+      const uint4 v = stage[stage_slot<GQ>(r, p)];
+      uint32_t *o = f.out + ((size_t)y * f.W + x) * f.B + g * G + 4 * r;
+      if (full) {
+        st_stream_v4(o, v.x, v.y, v.z, v.w);
+      } else {
+        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb)
+          if (g * G + 4 * r + bb < f.B) st_stream(o + bb, vv[bb]);
+      }
+    }
+  }
+  __syncwarp();  // the next row may overwrite the staging area
+}
+
 template <int G, int MMAX, bool TMA, bool VEC, bool LUT>
 __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorMap *tmap,
                                              unsigned int it, uint32_t epoch, Ctrl *ctrl,
                                              unsigned long long timeout_ns, uint8_t *s_tiles,
                                              uint32_t *s_row, uint32_t *s_ctot, uint64_t *s_bar,
-                                             const uint32_t *s_lut, uint32_t &phase) {
+                                             const uint32_t *s_lut, uint4 *s_stage, uint32_t &phase) {
   constexpr int GQ = G / 4;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -496,6 +552,8 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
               }
             }
           }
+        } else if (G >= 8 && s_stage != nullptr) {
+          emit_pixel_major_staged<G, VEC>(f, s_stage + (size_t)w * (kChunk * G / 4), acc, lane, c * kChunk, y, g);
         } else {
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -536,9 +594,11 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
   __shared__ unsigned int s_item, s_epoch;
   __shared__ uint32_t s_lut[LUT ? 256 : 1];
   const int NW = blockDim.x >> 5;
-  const SmemLayout L = smem_layout(NW, f.R, G, f.nchunks * f.gpc);
+  const bool stage = pm_staged(f.layout, G);
+  const SmemLayout L = smem_layout(NW, f.R, G, f.nchunks * f.gpc, stage);
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint4 *s_stage = stage ? reinterpret_cast<uint4 *>(base + L.stage_off) : nullptr;
   uint8_t *s_tiles = base + L.tile_off;
   uint32_t *s_row = reinterpret_cast<uint32_t *>(base + L.row_off);
   uint32_t *s_ctot = reinterpret_cast<uint32_t *>(base + L.ctot_off);
@@ -558,7 +618,7 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     __syncthreads();
     if (it >= f.nitems) break;
     process_item<G, MMAX, TMA, VEC, LUT>(f, &tmap, it, epoch, ctrl, timeout_ns, s_tiles, s_row, s_ctot,
-                                         s_bar, s_lut, phase);
+                                         s_bar, s_lut, s_stage, phase);
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -583,13 +643,13 @@ template <int G, int MMAX, bool TMA, bool VEC>
 __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     batch_kernel(const FrameDesc *frames, const CUtensorMap *__restrict__ tmaps,
                  const unsigned int *item_end, int nframes, int R_max,
-                 int nchunk_gpc_max, Ctrl *ctrl, unsigned long long timeout_ns) {
+                 int nchunk_gpc_max, int stage, Ctrl *ctrl, unsigned long long timeout_ns) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ unsigned int s_item, s_epoch;
   __shared__ int s_frame;
   __shared__ __align__(16) FrameDesc s_f;
   const int NW = blockDim.x >> 5;
-  const SmemLayout L = smem_layout(NW, R_max, G, nchunk_gpc_max);
+  const SmemLayout L = smem_layout(NW, R_max, G, nchunk_gpc_max, stage != 0);
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   uint8_t *s_tiles = base + L.tile_off;
@@ -627,8 +687,10 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     __syncthreads();
     if (t >= total) break;
     const unsigned int it = t - (fi > 0 ? ld_relaxed_u32(item_end + fi - 1) : 0u);
+    uint4 *s_stage = (stage != 0 && pm_staged(s_f.layout, G)) ? reinterpret_cast<uint4 *>(base + L.stage_off)
+                                                               : nullptr;
     process_item<G, MMAX, TMA, VEC, false>(s_f, tmaps + fi, it, epoch, ctrl, timeout_ns, s_tiles, s_row,
-                                           s_ctot, s_bar, nullptr, phase);
+                                           s_ctot, s_bar, nullptr, s_stage, phase);
     __syncthreads();
   }
   if (threadIdx.x == 0) {

@@ -36,6 +36,7 @@ EXPORTED = (
     "ihist_batch_items", "ihist_batch_destroy", "ihist_batch_query_all", "ihist_batch_upload_compute",
     "ihist_compute_noalloc", "ihist_plan_lut", "ihist_plan_edges", "ihist_plan_joint",
     "ihist_plan_channels", "ihist_window_search", "ihist_mapping_workspace_bytes", "ihist_mapping_compute",
+    "ihist_batch_get_tune",
 )
 
 
@@ -112,6 +113,8 @@ def load(path: str = LIB_PATH):
         fp = ctypes.POINTER(ihist_frame_t)
         L.ihist_batch_plan.argtypes = [fp, ci, ctypes.POINTER(ihist_tune_t), ctypes.POINTER(vp)]
         L.ihist_batch_plan.restype = ci
+        L.ihist_batch_get_tune.argtypes = [vp, ctypes.POINTER(ihist_tune_t)]
+        L.ihist_batch_get_tune.restype = ci
         L.ihist_batch_set_io.argtypes = [vp, fp, ci, vp]
         L.ihist_batch_set_io.restype = ci
         L.ihist_batch_compute.argtypes = [vp, vp]
@@ -323,6 +326,12 @@ def ihist_batch_plan(frames, tune=None) -> int:
     return out.value
 
 
+def ihist_batch_get_tune(batch: int) -> dict:
+    t = ihist_tune_t()
+    _check(load().ihist_batch_get_tune(batch, ctypes.byref(t)), "ihist_batch_get_tune")
+    return {k: getattr(t, k) for k in TUNE_FIELDS}
+
+
 def ihist_batch_set_io(batch: int, frames, stream: int = 0) -> None:
     arr = _frames_array(frames)
     _check(load().ihist_batch_set_io(batch, arr, len(frames), stream), "ihist_batch_set_io")
@@ -515,6 +524,7 @@ class Batch:
             from . import autotune
             tune = autotune.tune_batch([(f.shape[0], f.shape[1], b, l) for f, b, l in zip(self.frames, nb, ly)])
         self.handle = ihist_batch_plan(self._desc(), tune or None)
+        self.tune = ihist_batch_get_tune(self.handle)
 
     def _desc(self):
         d = []

@@ -42,7 +42,8 @@ MIXED = [(1, 1, 1, 0), (5, 3, 3, 1), (37, 131, 16, 0), (240, 320, 16, 0), (64, 2
 
 @pytest.mark.parametrize("tune", [None, {"rows_per_band": 8}, {"rows_per_band": 64, "bins_per_cta": 8},
                                   {"rows_per_band": 3, "ctas_per_sm": 1}, {"warps_per_cta": 8},
-                                  {"warps_per_cta": 8, "bins_per_cta": 8, "rows_per_band": 40}])
+                                  {"warps_per_cta": 8, "bins_per_cta": 8, "rows_per_band": 40},
+                                  {"bins_per_cta": 16}, {"bins_per_cta": 16, "rows_per_band": 9}])
 def test_mixed_batch(tune):
     imgs = [synth.uniform_frame(1000 + i, h, w) for i, (h, w, b, l) in enumerate(MIXED)]
     nbins = [b for (h, w, b, l) in MIXED]
@@ -224,3 +225,14 @@ def test_warps_per_cta_4_and_too_wide_frames_are_rejected():
     with pytest.raises(ihist.IhistError) as e:
         ihist.Batch([torch.zeros((16, 9000), dtype=torch.uint8, device="cuda")], [8])
     assert e.value.code == ihist.IHIST_ERR_UNSUPPORTED
+
+
+def test_pixel_major_batch_defaults_to_16_bin_groups():
+    shapes = [(240, 320, 16), (480, 640, 32), (720, 1280, 64), (37, 131, 100), (1, 1, 16)]
+    imgs = [synth.uniform_frame(3000 + i, h, w) for i, (h, w, b) in enumerate(shapes)]
+    nbins = [b for (h, w, b) in shapes]
+    with ihist.Batch([torch.from_numpy(x).cuda() for x in imgs], nbins, [1] * len(shapes)) as batch:
+        assert batch.tune["bins_per_cta"] == 16
+        batch.compute()
+        assert batch.status() == ihist.IHIST_OK
+        check_batch(batch, imgs, nbins, [1] * len(shapes))
