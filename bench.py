@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (640x480, uneven 256-frame batch, 8192x8192) "
                          "and the other bin structures (edges, joint RGB)")
+    ap.add_argument("--layout", choices=("bin", "pixel"), default="bin",
+                    help="output layout of the timed path (the workload's is bin-major; pixel for captures)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="simulated seconds of the serving workload per server mode (0 = skip)")
     ap.add_argument("--frames", type=int, default=64,
@@ -527,14 +529,16 @@ def main():
     d_frames = torch.from_numpy(frames).to(dev)
     # every frame queries the same rectangles: [frames][rects][4]
     d_rects = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(rects, (NFRAMES,) + rects.shape))).to(dev)
-    outs = torch.empty((NFRAMES, NBINS, H, W), dtype=torch.int32, device=dev)
+    layout = ihist.IHIST_PIXEL_MAJOR if args.layout == "pixel" else ihist.IHIST_BIN_MAJOR
+    outs = torch.empty((NFRAMES,) + ihist.out_shape(H, W, NBINS, layout), dtype=torch.int32, device=dev)
     d_query = torch.empty((NFRAMES * NRECTS * NBINS,), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     s = stream.cuda_stream
 
     # the batched form: one persistent launch over all 64 resident frames,
     # one launch for all 64 x 1000 region queries
-    batch = ihist.Batch([d_frames[f] for f in range(NFRAMES)], NBINS, outs=[outs[f] for f in range(NFRAMES)])
+    batch = ihist.Batch([d_frames[f] for f in range(NFRAMES)], NBINS, [layout] * NFRAMES,
+                        outs=[outs[f] for f in range(NFRAMES)])
     rp, qp = d_rects.data_ptr(), d_query.data_ptr()
 
     def step():
@@ -578,7 +582,7 @@ def main():
     resident_query = d_query.view(NFRAMES, NRECTS, NBINS)[NFRAMES - 1].cpu()
 
     # ---- plain per-frame launches (same frames, same outputs) ----
-    plan = ihist.Plan(H, W, NBINS, ihist.IHIST_BIN_MAJOR)
+    plan = ihist.Plan(H, W, NBINS, layout)
     pf_steps = max(3, min(args.steps, 20))
 
     def plain_step():
@@ -609,7 +613,7 @@ def main():
     h_frames = torch.from_numpy(frames).pin_memory()
     h_query = torch.empty((NFRAMES * NRECTS * NBINS,), dtype=torch.int32).pin_memory()
     d_in2 = torch.empty((NFRAMES, H, W), dtype=torch.uint8, device=dev)
-    halves = [ihist.Batch([d_in2[f] for f in range(g * half, (g + 1) * half)], NBINS,
+    halves = [ihist.Batch([d_in2[f] for f in range(g * half, (g + 1) * half)], NBINS, [layout] * half,
                           outs=[outs[f] for f in range(g * half, (g + 1) * half)]) for g in range(2)]
     copy_stream = torch.cuda.Stream(dev)
     hq = [h_frames[f] for f in range(NFRAMES)]
@@ -673,7 +677,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {
                 "workload": WORKLOAD, "frames_per_step": NFRAMES, "H": H, "W": W, "B": NBINS,
-                "layout": "bin-major", "queries_per_frame": NRECTS,
+                "layout": "bin-major" if layout == ihist.IHIST_BIN_MAJOR else "pixel-major",
+                "queries_per_frame": NRECTS,
                 "form": "batched: one persistent scan launch over the %d resident frames + one query launch" % NFRAMES,
                 "parallelism": "replicas (one independent 64-frame sequence per GPU)" if world > 1 else "single GPU",
                 "l2": "no flush: each step writes %.1f GB of output, > 129 MB L2" % (NFRAMES * H * W * NBINS * 4 / 1e9),
