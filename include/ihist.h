@@ -72,9 +72,11 @@ typedef struct ihist_plan_s *ihist_plan_t;
  *   ctas_per_sm     persistent grid = ctas_per_sm x SMs (0 = occupancy limit)
  *   timeout_us      limit of each carry wait before it gives up and latches
  *                   IHIST_ERR_LOOKBACK_TIMEOUT (default 2,000,000 us)
- *   fault_skip_band test hook, -1 = off: the CTAs of this band publish no
- *                   carries, so the band below must time out.  Used only
- *                   to test failure detection; never set it otherwise.
+ *   fault_skip_band test hook, 0 (or negative) = off: a value k >= 1
+ *                   makes the CTAs of band k-1 publish no carries, so the
+ *                   band below must time out (in every frame of a batch).
+ *                   Used only to test failure detection; never set it
+ *                   otherwise.  A zero-initialised struct leaves it off.
  *   warps_per_cta   batched launches: warps per CTA (4, 8 or 16; default
  *                   8 when every frame is at most 4096 columns wide, else
  *                   16).  A frame needs ceil(w/128) <= 4 x warps_per_cta.

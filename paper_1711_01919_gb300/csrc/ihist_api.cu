@@ -258,7 +258,7 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   p->ngsets = (ngroups + p->gpc - 1) / p->gpc;
   p->nitems = (unsigned int)p->nbands * (unsigned int)p->ngsets;
   p->timeout_us = t.timeout_us;
-  p->fault_skip_band = t.fault_skip_band;
+  p->fault_skip_band = t.fault_skip_band >= 1 ? t.fault_skip_band - 1 : -1;  // 1-based in the tune struct
   p->smem_bytes = smem_layout(p->NW, p->R, p->G, p->nchunks * p->gpc, pm_staged(layout, p->G)).bytes;
   const int occ = p->smem_bytes <= optin ? occupancy(fn, p->NW * 32, p->smem_bytes) : 0;
   if (occ < 1) {
@@ -395,7 +395,7 @@ extern "C" int ihist_plan_get_tune(ihist_plan_t p, ihist_tune_t *out) {
   out->chunks_per_warp = p->m;
   out->ctas_per_sm = p->ctas_per_sm;
   out->timeout_us = p->timeout_us;
-  out->fault_skip_band = p->fault_skip_band;
+  out->fault_skip_band = p->fault_skip_band + 1;  // 0 = off
   out->groups_per_cta = p->gpc;
   out->warps_per_cta = p->NW;
   return IHIST_OK;
@@ -704,6 +704,7 @@ bool frame_vec_ok(const ihist_frame_t &fr) {
 
 struct ihist_batch_s {
   int device, sms, cap, n, G, warps, mmax, R_req, R_max, ncg_max, ctas_cap, stage;
+  int fault_skip_band;  // test hook, -1 off
   int ctas_per_sm[2][2];  // occupancy of each (tma, vec) variant
   bool tma, vec;          // variant the current frames allow
   unsigned int timeout_us, total;
@@ -766,6 +767,7 @@ static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames, int n) {
     f.agg_cnt = b->slot_cnt[i];
     f.agg_left = b->slot_left[i];
     f.incl = b->slot_incl[i];
+    f.fault_skip_band = b->fault_skip_band;
     tma = tma && frame_tma_ok(fr);
     vec = vec && frame_vec_ok(fr);
     total += f.nitems;
@@ -865,6 +867,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   b->sms = sms;
   b->cap = n;
   b->G = t.bins_per_cta;
+  b->fault_skip_band = t.fault_skip_band >= 1 ? t.fault_skip_band - 1 : -1;
   // pixel-major frames stage their rows in shared memory
   b->stage = 0;
   for (int i = 0; i < n; ++i)
@@ -1068,7 +1071,7 @@ extern "C" int ihist_batch_get_tune(ihist_batch_t b, ihist_tune_t *out) {
   out->chunks_per_warp = b->mmax;
   out->ctas_per_sm = b->ctas_per_sm[1][1];
   out->timeout_us = b->timeout_us;
-  out->fault_skip_band = -1;
+  out->fault_skip_band = b->fault_skip_band + 1;  // 0 = off
   out->groups_per_cta = 0;  // chosen per frame
   out->warps_per_cta = b->warps;
   return IHIST_OK;

@@ -25,7 +25,7 @@ def _lib():
 def test_lookback_timeout_is_bounded_and_reported(skip_band):
     h, w, nbins = 64, 256, 8
     img = synth.uniform_frame(1, h, w)
-    tune = {"rows_per_band": 8, "fault_skip_band": skip_band, "timeout_us": 20000}
+    tune = {"rows_per_band": 8, "fault_skip_band": skip_band + 1, "timeout_us": 20000}  # 1-based hook
     with ihist.Plan(h, w, nbins, 0, tune=tune) as plan:
         d_img = torch.from_numpy(img).cuda()
         t0 = time.time()
@@ -54,7 +54,7 @@ def test_plan_recovers_after_timeout_launch():
     ref = oracle.integral_histogram(img, nbins)
     lib = ihist.load()
     import ctypes
-    t = ihist._tune_struct({"rows_per_band": 4, "fault_skip_band": 3, "timeout_us": 10000})
+    t = ihist._tune_struct({"rows_per_band": 4, "fault_skip_band": 4, "timeout_us": 10000})  # band 3
     hp = ctypes.c_void_p()
     assert lib.ihist_plan_tuned(h, w, nbins, 0, ctypes.byref(t), ctypes.byref(hp)) == 0
     d_img = torch.from_numpy(img).cuda()
@@ -68,3 +68,40 @@ def test_plan_recovers_after_timeout_launch():
             out = plan.compute(d_img)
             assert plan.status() == ihist.IHIST_OK
             assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(nbins, h, w), ref)
+
+
+def test_zeroed_tune_struct_leaves_the_fault_hook_off():
+    # a C caller's zero-initialised ihist_tune_t means defaults everywhere
+    import ctypes
+    lib = ihist.load()
+    h, w, nbins = 48, 200, 8
+    img = synth.uniform_frame(5, h, w)
+    t = ihist.ihist_tune_t()  # all zero
+    hp = ctypes.c_void_p()
+    assert lib.ihist_plan_tuned(h, w, nbins, 0, ctypes.byref(t), ctypes.byref(hp)) == 0
+    out = torch.empty((nbins, h, w), dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    ihist.ihist_compute(hp.value, torch.from_numpy(img).cuda().data_ptr(), w, out.data_ptr(), s)
+    assert ihist.ihist_status(hp.value, s) == ihist.IHIST_OK
+    assert ihist.ihist_plan_get_tune(hp.value)["fault_skip_band"] == 0
+    ihist.ihist_destroy(hp.value)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.integral_histogram(img, nbins))
+
+
+def test_batch_lookback_timeout_is_bounded_and_reported():
+    # band 1 of every frame publishes nothing: the frames' lower bands time out
+    imgs = [synth.uniform_frame(20 + i, h, w) for i, (h, w) in enumerate([(64, 256), (40, 700), (100, 130)])]
+    frames = [torch.from_numpy(x).cuda() for x in imgs]
+    tune = {"rows_per_band": 8, "fault_skip_band": 2, "timeout_us": 20000}
+    with ihist.Batch(frames, [8, 16, 4], tune=tune) as batch:
+        t0 = time.time()
+        batch.compute()
+        st = batch.status()
+        assert st == ihist.IHIST_ERR_LOOKBACK_TIMEOUT
+        assert time.time() - t0 < 5.0
+        assert batch.status() == ihist.IHIST_OK  # read-and-clear
+    with ihist.Batch(frames, [8, 16, 4], tune={"rows_per_band": 8}) as batch:
+        batch.compute()
+        assert batch.status() == ihist.IHIST_OK
+        for x, o, b in zip(imgs, batch.outs, [8, 16, 4]):
+            assert np.array_equal(o.cpu().numpy().view(np.uint32).reshape(b, *x.shape), oracle.integral_histogram(x, b))
