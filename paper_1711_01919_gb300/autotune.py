@@ -68,9 +68,12 @@ def plan_candidates(h: int, w: int, nbins: int):
     return out
 
 
-def batch_candidates():
+def batch_candidates(shapes=()):
+    """Batch launch shapes to time (the default first); 16-bin groups too
+    when some frame is pixel-major (their longer pieces of pixel records)."""
+    gs = (4, 8, 16) if any(s[3] == ihist.IHIST_PIXEL_MAJOR for s in shapes) else (4, 8)
     return [{}] + [{"warps_per_cta": nw, "bins_per_cta": G, "rows_per_band": R}
-                   for nw in (8, 16) for G in (4, 8) for R in (24, 32, 40, 48, 56)]
+                   for nw in (8, 16) for G in gs for R in (24, 32, 40, 48, 56)]
 
 
 def _device_key():
@@ -164,7 +167,7 @@ def tune_batch(shapes, timer=None, device=None, use_cache=True):
         if key in cache:
             return cache[key]["tune"]
     timer = timer or (lambda t: time_batch(shapes, t))
-    best, ms, _ = _search(batch_candidates(), timer)
+    best, ms, _ = _search(batch_candidates(shapes), timer)
     if use_cache:
         with _lock:
             cache = _load_cache(path)

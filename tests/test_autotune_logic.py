@@ -54,3 +54,12 @@ def test_batch_tuning_key_and_cache(tmp_path, monkeypatch):
 def test_choose_layout():
     assert autotune.choose_layout(10, 10, 4, timer=lambda l: 2.0 if l == 0 else 1.0) == ihist.IHIST_PIXEL_MAJOR
     assert autotune.choose_layout(10, 10, 4, timer=lambda l: 1.0 if l == 0 else 2.0) == ihist.IHIST_BIN_MAJOR
+
+
+def test_batch_candidates_add_16_bin_groups_for_pixel_major():
+    bm = autotune.batch_candidates([(240, 320, 16, 0)])
+    pm = autotune.batch_candidates([(240, 320, 16, 0), (480, 640, 32, 1)])
+    assert bm[0] == {} and pm[0] == {}
+    assert not any(t.get("bins_per_cta") == 16 for t in bm)
+    assert any(t.get("bins_per_cta") == 16 for t in pm)
+    assert len(pm) > len(bm)
