@@ -49,7 +49,9 @@ enum {
   IHIST_ERR_OOM = 3,              /* workspace allocation failed */
   IHIST_ERR_CUDA = 4,             /* a CUDA runtime call failed */
   IHIST_ERR_LOOKBACK_TIMEOUT = 5, /* device: a carry wait ran out of time (result invalid) */
-  IHIST_ERR_BAD_RECT = 6          /* device: a query rectangle was out of range (its row is zero) */
+  IHIST_ERR_BAD_RECT = 6,         /* device: a query rectangle was out of range (its row is zero) */
+  IHIST_ERR_CHECK_FAILED = 7      /* device, checked builds only: an out-of-range access was caught and
+                                     skipped (result invalid; a library bug) */
 };
 
 /* Output layouts of H.  Bin-major is the paper's b x h x w tensor mapped

@@ -93,6 +93,7 @@ extern "C" const char *ihist_error_string(int code) {
     case IHIST_ERR_CUDA: return "CUDA runtime error";
     case IHIST_ERR_LOOKBACK_TIMEOUT: return "carry look-back wait timed out; result invalid";
     case IHIST_ERR_BAD_RECT: return "query rectangle out of range; its histogram is zero";
+    case IHIST_ERR_CHECK_FAILED: return "checked build caught an out-of-range access; result invalid";
     default: return "unknown status";
   }
 }

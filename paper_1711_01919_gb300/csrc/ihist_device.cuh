@@ -17,7 +17,7 @@ constexpr uint32_t kFull = 0xffffffffu;
 enum : uint32_t { kStateAgg = 1u, kStateIncl = 2u, kStatePoison = 3u };
 
 // Device status codes (mirror the IHIST_* values of ihist.h).
-enum : int { kStatusOk = 0, kStatusTimeout = 5, kStatusBadRect = 6 };
+enum : int { kStatusOk = 0, kStatusTimeout = 5, kStatusBadRect = 6, kStatusCheck = 7 };
 
 // Per-plan control block in device memory (zeroed once at plan creation).
 struct Ctrl {
@@ -28,6 +28,16 @@ struct Ctrl {
   unsigned int timeouts;  // number of waits that gave up
   unsigned int pad[3];
 };
+
+// Checked builds (compiled with -DIHIST_CHECKED, the stand-in for a memory
+// sanitizer): each guarded access is tested first; a failed test latches
+// kStatusCheck in the status word and the access is skipped.  Other builds
+// compile the guards away.
+#ifdef IHIST_CHECKED
+#define IHIST_GUARD(ctrl, cond) ::ihist::guard_access((ctrl), (cond))
+#else
+#define IHIST_GUARD(ctrl, cond) true
+#endif
 
 __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
   uint32_t v;
@@ -105,6 +115,11 @@ __device__ __forceinline__ uint32_t warp_scan_incl(uint32_t v, int lane) {
 // Latch the first device error into the status word.
 __device__ __forceinline__ void latch_status(Ctrl *ctrl, int code) {
   atomicCAS(&ctrl->status, kStatusOk, code);
+}
+
+__device__ __forceinline__ bool guard_access(Ctrl *ctrl, bool ok) {
+  if (!ok) latch_status(ctrl, kStatusCheck);
+  return ok;
 }
 
 // Wait (all lanes of a warp, same address) until the flag carries this

@@ -191,7 +191,10 @@ __device__ __forceinline__ int stage_slot(int r, int p) {
 // contiguous words, so a warp store covers 32/(G/4) records in full pieces.
 template <int G, bool VEC>
 __device__ __forceinline__ void emit_pixel_major_staged(const FrameDesc &f, uint4 *stage, const uint32_t (&acc)[G][4],
-                                                        int lane, int cbase, int y, int g) {
+                                                        int lane, int cbase, int y, int g, Ctrl *ctrl) {
+  const uint32_t *out_end = f.out + (size_t)f.H * f.W * f.B;
+  (void)out_end;
+  (void)ctrl;
   constexpr int GQ = G / 4;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -211,12 +214,13 @@ __device__ __forceinline__ void emit_pixel_major_staged(const FrameDesc &f, uint
       const uint4 v = stage[stage_slot<GQ>(r, p)];
       uint32_t *o = f.out + ((size_t)y * f.W + x) * f.B + g * G + 4 * r;
       if (full) {
-        st_stream_v4(o, v.x, v.y, v.z, v.w);
+        if (IHIST_GUARD(ctrl, o >= f.out && o + 4 <= out_end)) st_stream_v4(o, v.x, v.y, v.z, v.w);
       } else {
         const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int bb = 0; bb < 4; ++bb)
-          if (g * G + 4 * r + bb < f.B) st_stream(o + bb, vv[bb]);
+          if (g * G + 4 * r + bb < f.B && IHIST_GUARD(ctrl, o + bb >= f.out && o + bb < out_end))
+            st_stream(o + bb, vv[bb]);
       }
     }
   }
@@ -234,6 +238,8 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
   const int w = threadIdx.x >> 5;
   const int k = (int)(it / (unsigned)f.ngsets);
   const int gs = (int)(it % (unsigned)f.ngsets);
+  // checked builds: the item must lie inside the frame (uniform over the CTA)
+  if (!IHIST_GUARD(ctrl, k < f.nbands && gs < f.ngsets)) return;
   const int lg = w / f.wpg;  // local bin group of this warp
   const int wg = w % f.wpg;  // warp slot within the group
   const int g = gs * f.gpc + lg;
@@ -246,6 +252,10 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
   const int my_m = gvalid ? max(0, min(f.m, f.nchunks - c_begin)) : 0;  // warp-uniform
   const bool publish = (k != f.fault_skip_band);
   const unsigned int ci0 = ((unsigned)k * f.ngroups + g) * (unsigned)f.nchunks;  // chunk 0
+  const unsigned int nci = (unsigned)f.nbands * f.ngroups * f.nchunks;  // carry slots of the frame
+  const uint32_t *out_end = f.out + (size_t)f.H * f.W * f.B;           // end of the frame's H
+  (void)nci;
+  (void)out_end;
   uint32_t *my_ctot = s_ctot + (size_t)(gvalid ? lg : 0) * f.nchunks * G;
   uint8_t *tile = s_tiles + (size_t)w * f.R * kChunk;
   uint64_t *bar = s_bar + w;
@@ -325,6 +335,7 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
       }
       // aggregate: this band's column counts, [128 cols][GQ] words
       uint32_t *dst = f.agg_cnt + ((size_t)(ci0 + c) * kChunk + 4 * lane) * GQ;
+      if (!IHIST_GUARD(ctrl, ci0 + c < nci)) continue;
 #pragma unroll
       for (int j = 0; j < GQ; ++j) {
         // words 4j..4j+3 of this lane's 4*GQ words: col (4j+t)/GQ, group (4j+t)%GQ
@@ -365,6 +376,7 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
   // ---- publish aggregates (all chunks first: they depend on no one) ----
   for (int cc = 0; cc < my_m; ++cc) {
     const int c = c_begin + cc;
+    if (!IHIST_GUARD(ctrl, ci0 + c < nci)) continue;
     if (lane < G) f.agg_left[(size_t)(ci0 + c) * G + lane] = my_ctot[(size_t)c * G + lane];
     __threadfence();
     __syncwarp();
@@ -377,6 +389,7 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
     const int c = c_begin + cc;
     const unsigned int ci = ci0 + c;
     const int x = c * kChunk + 4 * lane;
+    if (!IHIST_GUARD(ctrl, ci < nci)) continue;
 
     uint32_t left[G];  // band-count sums left of the chunk, from aggregates
     uint32_t s16[GQ][4][2];
@@ -396,6 +409,10 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
     // when the band just above has usually published already).
     for (int j = k - 1; j >= 0 && !poisoned; --j) {
       const unsigned int cj = ((unsigned)j * f.ngroups + g) * (unsigned)f.nchunks + c;
+      if (!IHIST_GUARD(ctrl, cj < nci)) {
+        poisoned = true;
+        break;
+      }
       const uint32_t st = wait_flag(f.flags + cj, epoch, ctrl, timeout_ns);
       if (st == kStatePoison) {
         poisoned = true;
@@ -544,16 +561,19 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
           for (int b = 0; b < G; ++b, o += plane) {
             if (g * G + b < f.B) {
               if (VEC) {
-                if (x < f.W) st_stream_v4(o, acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+                if (x < f.W && IHIST_GUARD(ctrl, o >= f.out && o + 4 <= out_end))
+                  st_stream_v4(o, acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
               } else {
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                  if (x + i < f.W) st_stream(o + i, acc[b][i]);
+                  if (x + i < f.W && IHIST_GUARD(ctrl, o + i >= f.out && o + i < out_end))
+                    st_stream(o + i, acc[b][i]);
               }
             }
           }
         } else if (G >= 8 && s_stage != nullptr) {
-          emit_pixel_major_staged<G, VEC>(f, s_stage + (size_t)w * (kChunk * G / 4), acc, lane, c * kChunk, y, g);
+          emit_pixel_major_staged<G, VEC>(f, s_stage + (size_t)w * (kChunk * G / 4), acc, lane, c * kChunk, y, g,
+                                          ctrl);
         } else {
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -562,12 +582,15 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
 #pragma unroll
               for (int b4 = 0; b4 < GQ; ++b4) {
                 if (VEC && (f.B & 3) == 0 && g * G + 4 * b4 + 4 <= f.B) {
-                  st_stream_v4(o + 4 * b4, acc[4 * b4][i], acc[4 * b4 + 1][i], acc[4 * b4 + 2][i],
-                               acc[4 * b4 + 3][i]);
+                  if (IHIST_GUARD(ctrl, o + 4 * b4 >= f.out && o + 4 * b4 + 4 <= out_end))
+                    st_stream_v4(o + 4 * b4, acc[4 * b4][i], acc[4 * b4 + 1][i], acc[4 * b4 + 2][i],
+                                 acc[4 * b4 + 3][i]);
                 } else {
 #pragma unroll
                   for (int bb = 0; bb < 4; ++bb)
-                    if (g * G + 4 * b4 + bb < f.B) st_stream(o + 4 * b4 + bb, acc[4 * b4 + bb][i]);
+                    if (g * G + 4 * b4 + bb < f.B &&
+                        IHIST_GUARD(ctrl, o + 4 * b4 + bb >= f.out && o + 4 * b4 + bb < out_end))
+                      st_stream(o + 4 * b4 + bb, acc[4 * b4 + bb][i]);
                 }
               }
             }

@@ -7,7 +7,9 @@ Non-zero return codes raise :class:`IhistError`.  ``Plan`` adds the torch
 plumbing (output allocation, stream lookup) around the same calls.
 
 There is no fallback: if libihist.so is missing the import of this module
-succeeds but the first call raises, naming the build step.
+succeeds but the first call raises, naming the build step.  The environment
+variable IHIST_LIB selects another build of the same library (for example
+libihist_checked.so, whose kernels guard every carry index and output store).
 """
 from __future__ import annotations
 
@@ -16,7 +18,7 @@ import os
 import threading
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libihist.so")
+LIB_PATH = os.environ.get("IHIST_LIB") or os.path.join(PKG, "libihist.so")
 
 IHIST_OK = 0
 IHIST_ERR_INVALID_ARG = 1
@@ -25,6 +27,7 @@ IHIST_ERR_OOM = 3
 IHIST_ERR_CUDA = 4
 IHIST_ERR_LOOKBACK_TIMEOUT = 5
 IHIST_ERR_BAD_RECT = 6
+IHIST_ERR_CHECK_FAILED = 7
 IHIST_BIN_MAJOR = 0
 IHIST_PIXEL_MAJOR = 1
 

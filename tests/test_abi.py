@@ -38,7 +38,7 @@ def test_output_bytes_and_error_strings(lib):
     assert ihist.ihist_output_bytes(1080, 1920, 64) == 530841600
     assert ihist.ihist_output_bytes(8192, 8192, 128) == 34359738368
     assert ihist.ihist_output_bytes(0, 5, 5) == 0
-    for code in range(7):
+    for code in range(8):
         assert ihist.ihist_error_string(code) and ihist.ihist_error_string(code) != "unknown status"
     assert ihist.ihist_error_string(99) == "unknown status"
 
