@@ -357,12 +357,16 @@ class GpuExecutor:
     are returned to it on eviction.
     """
 
-    def __init__(self, mode="batched", nslots=64, max_shape=(1080, 1920, 64), query_slots=8, max_rects=10000):
+    def __init__(self, mode="batched", nslots=64, max_shape=(1080, 1920, 64), query_slots=8, max_rects=10000,
+                 trace=False):
+        """trace: mark every launch with an NVTX range (frames / query, with
+        sizes) so a profiler's timeline shows the serving loop's issue."""
         import torch
 
         from . import ihist
         self.torch, self.ih = torch, ihist
         self.mode = mode
+        self.trace = trace
         self.stream = torch.cuda.current_stream()
         self.copy = torch.cuda.Stream()
         self.qstream = torch.cuda.Stream(priority=-1)
@@ -444,6 +448,15 @@ class GpuExecutor:
         return p
 
     def launch_frames(self, reqs, t):
+        if self.trace:
+            self.torch.cuda.nvtx.range_push("ihist frames n=%d" % len(reqs))
+        try:
+            return self._launch_frames(reqs, t)
+        finally:
+            if self.trace:
+                self.torch.cuda.nvtx.range_pop()
+
+    def _launch_frames(self, reqs, t):
         torch, ih = self.torch, self.ih
         outs = {r.rid: torch.empty((r.nbins, r.h, r.w), dtype=torch.int32, device="cuda") for r in reqs}
         ev = torch.cuda.Event(enable_timing=True)
@@ -473,6 +486,15 @@ class GpuExecutor:
         return {"ev": ev, "payloads": {r.rid: (outs[r.rid], r.h, r.w, r.nbins) for r in reqs}}
 
     def launch_query(self, q, payload, t):
+        if self.trace:
+            self.torch.cuda.nvtx.range_push("ihist query rects=%d" % len(q.rects))
+        try:
+            return self._launch_query(q, payload, t)
+        finally:
+            if self.trace:
+                self.torch.cuda.nvtx.range_pop()
+
+    def _launch_query(self, q, payload, t):
         # the server launches a query only once its histogram is complete,
         # and keeps the histogram resident until the query is done
         torch, ih = self.torch, self.ih
@@ -514,7 +536,7 @@ class GpuExecutor:
 
 
 def serve(mode="batched", duration_s=2.0, budget_gb=40.0, seed=None, frame_rate=2000.0, query_rate=200.0,
-          rects_per_query=10000, pool_per_shape=8, saturate=False):
+          rects_per_query=10000, pool_per_shape=8, saturate=False, trace=False):
     """Run the serving workload on the GPU; returns the server's report."""
     import torch
     seed = synth.workload_seed(4) if seed is None else seed
@@ -527,7 +549,7 @@ def serve(mode="batched", duration_s=2.0, budget_gb=40.0, seed=None, frame_rate=
         # the same requests, arriving 1000 times faster than the server can take them
         for r in reqs:
             r.t_arrival *= 1e-3
-    ex = GpuExecutor(mode, max_rects=max(1, rects_per_query))
+    ex = GpuExecutor(mode, max_rects=max(1, rects_per_query), trace=trace)
     ex.warm(sorted({(r.h, r.w, r.nbins) for r in reqs if isinstance(r, FrameRequest)}))
     srv = Server(ex, int(budget_gb * (1 << 30)), mode=mode, keep_results=False)
     ex.start()

@@ -235,3 +235,14 @@ def test_query_edge_rectangles_and_bad_rect_status():
             assert plan.status() == ihist.IHIST_OK  # read-and-clear
             z = plan.query(out, torch.zeros((0, 4), dtype=torch.int32, device="cuda"))
             assert z.shape == (0, nbins)
+
+
+@pytest.mark.parametrize("h,w,nbins,layout", [(9, 16384, 5, 0), (9, 16384, 5, 1), (65535, 3, 2, 0), (65535, 3, 2, 1),
+                                              (40, 300, 256, 1), (3, 8192, 256, 0), (1, 16384, 1, 0)])
+def test_extreme_shapes(h, w, nbins, layout):
+    # the widest frame a plan takes (16384 columns), the tallest (65535 rows)
+    # and 256 bins in both layouts
+    img = synth.uniform_frame(h + 3 * w + nbins, h, w)
+    got = run_gpu(img, nbins, layout=layout)
+    assert_same(got, to_layout(oracle.integral_histogram(img, nbins), layout),
+                "%dx%d B=%d layout %d" % (h, w, nbins, layout))

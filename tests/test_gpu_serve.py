@@ -27,7 +27,7 @@ def run_server(mode, duration=0.04, budget_gb=40.0, saturate=False):
     if saturate:
         for r in reqs:
             r.t_arrival = 0.0
-    ex = serve.GpuExecutor(mode, nslots=16)
+    ex = serve.GpuExecutor(mode, nslots=16, trace=True)  # NVTX ranges must not disturb anything
     ex.warm(sorted({(r.h, r.w, r.nbins) for r in reqs if isinstance(r, serve.FrameRequest)}))
     srv = serve.Server(ex, int(budget_gb * (1 << 30)), max_batch=16, mode=mode)
     ex.start()
