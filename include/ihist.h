@@ -194,11 +194,16 @@ int ihist_query(ihist_plan_t plan, const uint32_t *d_hist, const int32_t *d_rect
  *             (pixel-major reads each corner as one contiguous vector and is
  *             the faster layout here)
  *   d_target  nbins uint32 counts, device
- *   d_scores  ny * nx uint32, row-major [i][j], device
- * IHIST_ERR_INVALID_ARG if the window does not fit the frame or stride < 1.
- * Asynchronous on stream; allocates nothing. */
+ *   d_scores  ny * nx uint32, row-major [i][j], device; may be NULL
+ *   d_best    one uint64, device, 8-byte aligned; may be NULL: receives the
+ *             best window as (score << 32) | (0xffffffff - (i * nx + j)),
+ *             the highest score and among equal scores the first window in
+ *             row-major order (0 if there is none); the call clears it first
+ * At least one of d_scores and d_best must be given.  IHIST_ERR_INVALID_ARG
+ * if the window does not fit the frame or stride < 1.  Asynchronous on
+ * stream; allocates nothing. */
 int ihist_window_search(ihist_plan_t plan, const uint32_t *d_hist, const uint32_t *d_target, int win_h,
-                        int win_w, int stride, uint32_t *d_scores, void *stream);
+                        int win_w, int stride, uint32_t *d_scores, unsigned long long *d_best, void *stream);
 
 /* The paper's own GPU mappings, rebuilt on this GPU as comparison kernels
  * for measuring the fused look-back design against them (not a fast path):

@@ -529,13 +529,17 @@ extern "C" int ihist_query(ihist_plan_t p, const uint32_t *d_hist, const int32_t
 }
 
 extern "C" int ihist_window_search(ihist_plan_t p, const uint32_t *d_hist, const uint32_t *d_target, int win_h,
-                                   int win_w, int stride, uint32_t *d_scores, void *stream) {
-  if (!p || !d_hist || !d_target || !d_scores) return IHIST_ERR_INVALID_ARG;
+                                   int win_w, int stride, uint32_t *d_scores, unsigned long long *d_best,
+                                   void *stream) {
+  if (!p || !d_hist || !d_target || (!d_scores && !d_best)) return IHIST_ERR_INVALID_ARG;
   if (win_h < 1 || win_w < 1 || win_h > p->H || win_w > p->W || stride < 1) return IHIST_ERR_INVALID_ARG;
-  if (((uintptr_t)d_hist & 3u) || ((uintptr_t)d_target & 3u) || ((uintptr_t)d_scores & 3u))
+  if (((uintptr_t)d_hist & 3u) || ((uintptr_t)d_target & 3u) || ((uintptr_t)d_scores & 3u) ||
+      ((uintptr_t)d_best & 7u))
     return IHIST_ERR_INVALID_ARG;
   int rc = check_device(p);
   if (rc != IHIST_OK) return rc;
+  if (d_best && cudaMemsetAsync(d_best, 0, sizeof(unsigned long long), (cudaStream_t)stream) != cudaSuccess)
+    return IHIST_ERR_CUDA;
   const int ny = (p->H - win_h) / stride + 1, nx = (p->W - win_w) / stride + 1;
   const long long total = (long long)ny * nx;
   const unsigned int threads = 256;
@@ -544,13 +548,22 @@ extern "C" int ihist_window_search(ihist_plan_t p, const uint32_t *d_hist, const
   if (p->layout == IHIST_BIN_MAJOR) {
     const unsigned int grid =
         (unsigned int)std::min<long long>((total + threads - 1) / threads, (long long)p->sms * 8);
-    window_kernel_bin_major<<<grid, threads, smem, s>>>(d_hist, p->H, p->W, p->B, d_target, win_h, win_w, stride,
-                                                        ny, nx, d_scores);
+    // the map-only search keeps the plain kernel (no best-window tracking in its loop)
+    if (d_best)
+      window_kernel_bin_major<true><<<grid, threads, smem, s>>>(d_hist, p->H, p->W, p->B, d_target, win_h, win_w,
+                                                                stride, ny, nx, d_scores, d_best);
+    else
+      window_kernel_bin_major<false><<<grid, threads, smem, s>>>(d_hist, p->H, p->W, p->B, d_target, win_h, win_w,
+                                                                 stride, ny, nx, d_scores, nullptr);
   } else {
     const unsigned int grid =
         (unsigned int)std::min<long long>((total + threads / 32 - 1) / (threads / 32), (long long)p->sms * 8);
-    window_kernel_pixel_major<<<grid, threads, smem, s>>>(d_hist, p->H, p->W, p->B, d_target, win_h, win_w,
-                                                          stride, ny, nx, d_scores);
+    if (d_best)
+      window_kernel_pixel_major<true><<<grid, threads, smem, s>>>(d_hist, p->H, p->W, p->B, d_target, win_h, win_w,
+                                                                  stride, ny, nx, d_scores, d_best);
+    else
+      window_kernel_pixel_major<false><<<grid, threads, smem, s>>>(d_hist, p->H, p->W, p->B, d_target, win_h,
+                                                                   win_w, stride, ny, nx, d_scores, nullptr);
   }
   if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
   return IHIST_OK;
@@ -873,19 +886,20 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   b->stage = 0;
   for (int i = 0; i < n; ++i)
     if (pm_staged(frames[i].layout, b->G)) b->stage = 1;
-  // default: 8-warp CTAs (4 per SM overlap their count, look-back and emit
-  // phases better than 2 of 16 warps: measured 5% faster on 1080p frames)
-  // when every frame fits 8 warps x 4 chunks, else 16 warps
+  const int max_m = b->G == 16 ? 2 : 4;  // chunks per warp the instantiations cover
   b->warps = t.warps_per_cta;
   if (b->warps == 0) {
-    // 16-warp CTAs for pixel-major batches (staged rows: 10.5 against 11.7 ms
-    // for 64 pixel-major 1080p frames)
-    b->warps = b->stage ? kBatchWarps : 8;
+    // 8-warp CTAs (4 per SM overlap their count, look-back and emit phases
+    // better than 2 of 16 warps: 5% faster on 1080p frames), except 16 for
+    // staged pixel-major rows in 8-bin groups (64 pixel-major 1080p frames:
+    // 8 bins 10.5 ms with 16 warps against 11.7 with 8; 16 bins 8.2 ms with
+    // 8 warps against 8.5 with 16) and for frames wider than 8 warps x
+    // max_m chunks
+    b->warps = (b->stage && b->G != 16) ? kBatchWarps : 8;
     for (int i = 0; i < n; ++i)
-      if (frames[i].w > 8 * 4 * kChunk) b->warps = kBatchWarps;
+      if (frames[i].w > 8 * max_m * kChunk) b->warps = kBatchWarps;
   }
   b->timeout_us = t.timeout_us ? t.timeout_us : kDefaultTimeoutUs;
-  const int max_m = b->G == 16 ? 2 : 4;  // chunks per warp the instantiations cover
   // every kernel variant the batch may launch may use the opt-in shared memory
   for (int mm = 1; mm <= max_m; mm <<= 1)
     for (int tma = 0; tma < 2; ++tma)

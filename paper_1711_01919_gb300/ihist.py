@@ -150,7 +150,7 @@ def load(path: str = LIB_PATH):
         L.ihist_mapping_workspace_bytes.restype = sz
         L.ihist_mapping_compute.argtypes = [ci, ci, ci, ci, vp, sz, vp, vp, vp]
         L.ihist_mapping_compute.restype = ci
-        L.ihist_window_search.argtypes = [vp, vp, vp, ci, ci, ci, vp, vp]
+        L.ihist_window_search.argtypes = [vp, vp, vp, ci, ci, ci, vp, vp, vp]
         L.ihist_window_search.restype = ci
         L.ihist_plan_channels.argtypes = [vp]
         L.ihist_plan_channels.restype = ci
@@ -257,9 +257,9 @@ def ihist_query(plan: int, d_hist: int, d_rects: int, n: int, d_hist_out: int, s
 
 
 def ihist_window_search(plan: int, d_hist: int, d_target: int, win_h: int, win_w: int, stride: int,
-                        d_scores: int, stream: int = 0) -> None:
-    _check(load().ihist_window_search(plan, d_hist, d_target, win_h, win_w, stride, d_scores, stream),
-           "ihist_window_search")
+                        d_scores: int, d_best: int = 0, stream: int = 0) -> None:
+    _check(load().ihist_window_search(plan, d_hist, d_target, win_h, win_w, stride, d_scores or None,
+                                      d_best or None, stream), "ihist_window_search")
 
 
 IHIST_MAPPING_CW_STS, IHIST_MAPPING_CW_TIS, IHIST_MAPPING_WF_TIS = 1, 2, 3
@@ -478,8 +478,24 @@ class Plan:
         if out is None:
             out = torch.empty((max(ny, 0), max(nx, 0)), dtype=torch.int32, device=target.device)
         ihist_window_search(self.handle, hist.data_ptr(), target.data_ptr(), win_h, win_w, stride, out.data_ptr(),
-                            _stream(stream))
+                            0, _stream(stream))
         return out
+
+    def window_best(self, hist, target, win_h: int, win_w: int, stride: int, stream=None):
+        """(score, i, j) of the best window of the search (highest score, the
+        first in row-major order among ties); no score map is written."""
+        import torch
+        if target.dtype != torch.int32 or not target.is_contiguous() or target.numel() != self.nbins:
+            raise ValueError("target must be a contiguous int32 tensor of nbins counts")
+        best = torch.zeros(1, dtype=torch.int64, device=target.device)
+        ihist_window_search(self.handle, hist.data_ptr(), target.data_ptr(), win_h, win_w, stride, 0,
+                            best.data_ptr(), _stream(stream))
+        v = int(best.item()) & 0xffffffffffffffff
+        if v == 0:
+            return None
+        _, nx = window_grid(self.h, self.w, win_h, win_w, stride)
+        idx = 0xffffffff - (v & 0xffffffff)
+        return v >> 32, idx // nx, idx % nx
 
     def status(self, stream=None) -> int:
         return ihist_status(self.handle, _stream(stream))

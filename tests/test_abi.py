@@ -101,7 +101,7 @@ def test_other_bin_structures_reject_bad_arguments_before_touching_cuda(lib):
 
 
 def test_window_search_rejects_null_plan(lib):
-    assert lib.ihist_window_search(None, None, None, 1, 1, 1, None, None) == ihist.IHIST_ERR_INVALID_ARG
+    assert lib.ihist_window_search(None, None, None, 1, 1, 1, None, None, None) == ihist.IHIST_ERR_INVALID_ARG
     assert ihist.window_grid(1080, 1920, 64, 64, 4) == (255, 465)
     assert ihist.window_grid(10, 10, 10, 10, 3) == (1, 1)
 

@@ -35,8 +35,12 @@ def test_window_search_matches_oracle(layout, h, w, nbins, wh, ww, st):
     with ihist.Plan(h, w, nbins, layout) as plan:
         hist = plan.compute(torch.from_numpy(img).cuda())
         got = plan.window_search(hist, torch.from_numpy(target).cuda(), wh, ww, st)
+        best = plan.window_best(hist, torch.from_numpy(target).cuda(), wh, ww, st)
         assert plan.status() == ihist.IHIST_OK
     assert np.array_equal(got.cpu().numpy().view(np.uint32), exp)
+    # numpy's argmax takes the first of equal maxima in row-major order, as the kernel must
+    k = int(np.argmax(exp))
+    assert best == (int(exp.max()), k // exp.shape[1], k % exp.shape[1])
 
 
 def test_window_search_1080p_tracks_the_planted_patch():
@@ -55,6 +59,11 @@ def test_window_search_1080p_tracks_the_planted_patch():
             assert plan.status() == ihist.IHIST_OK
         assert np.array_equal(got, exp), layout
         assert got[y // 8, x // 8] == 64 * 64
+        with ihist.Plan(h, w, nbins, layout) as plan:
+            hist = plan.compute(torch.from_numpy(img).cuda())
+            best = plan.window_best(hist, torch.from_numpy(target).cuda(), 64, 64, 8)
+        k = int(np.argmax(exp))
+        assert best == (64 * 64, k // exp.shape[1], k % exp.shape[1])
 
 
 def test_window_search_rejects_bad_windows():
