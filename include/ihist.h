@@ -65,7 +65,10 @@ typedef struct ihist_plan_s *ihist_plan_t;
 /* Tile shape of the fused scan kernel.  Zero fields take the library's
  * default for the frame shape.
  *   rows_per_band   R, rows one CTA owns (1..255)
- *   bins_per_cta    G, bins one CTA owns (4, 8 or 16; default 4)
+ *   bins_per_cta    G, bins one CTA owns (4, 8 or 16; default 4, or for
+ *                   pixel-major output 16 (8 with fewer than 16 bins or
+ *                   more than 4096 columns): longer contiguous pieces of
+ *                   each pixel's record)
  *   chunks_per_warp m, 128-column chunks one warp owns (1, 2, 4 or 8;
  *                   at most 2 with bins_per_cta 16)
  *   groups_per_cta  bin groups one CTA serves side by side (warps = groups
@@ -80,8 +83,10 @@ typedef struct ihist_plan_s *ihist_plan_t;
  *                   Used only to test failure detection; never set it
  *                   otherwise.  A zero-initialised struct leaves it off.
  *   warps_per_cta   batched launches: warps per CTA (4, 8 or 16; default
- *                   8 when every frame is at most 4096 columns wide, else
- *                   16).  A frame needs ceil(w/128) <= 4 x warps_per_cta.
+ *                   8, or 16 for pixel-major batches with 8 bins per CTA
+ *                   and for frames wider than 8 warps can cover).  A frame
+ *                   needs ceil(w/128) <= 4 x warps_per_cta (2 x with 16
+ *                   bins per CTA).
  *                   Plans derive it from the tiling, ignore it on input
  *                   and report it in ihist_plan_get_tune.                 */
 typedef struct {
