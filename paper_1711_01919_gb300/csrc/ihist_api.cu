@@ -1,6 +1,6 @@
-// ihist_api.cu -- host side of libihist.so: argument validation, plan and
-// workspace management, kernel selection and launches.  Declared in
-// include/ihist.h.
+// ihist_api.cu -- host side of libihist.so for single-frame plans: argument
+// validation, plan and workspace management, kernel selection and launches
+// (batches are in ihist_batch_api.cu).  Declared in include/ihist.h.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "ihist.h"
+#include "ihist_host.h"
 #include "ihist_joint.cuh"
 #include "ihist_kernels.h"
 #include "ihist_query.cuh"
@@ -20,13 +21,9 @@
 
 using namespace ihist;
 
-namespace {
+using namespace ihist::host;
 
-int mmax_for(int m) { return m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : 8; }
-
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
-// (no link-time dependency on libcuda).
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+PFN_cuTensorMapEncodeTiled_v12000 ihist::host::tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -40,12 +37,6 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   }();
   return fn;
 }
-
-constexpr unsigned int kDefaultTimeoutUs = 2000000u;
-
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-}  // namespace
 
 enum Binning { kUniform = 0, kTable = 1, kJoint = 2 };
 
@@ -98,7 +89,7 @@ extern "C" const char *ihist_error_string(int code) {
   }
 }
 
-static int validate_shape(int h, int w, int nbins, int layout) {
+int ihist::host::validate_shape(int h, int w, int nbins, int layout) {
   if (h < 1 || w < 1 || h > 65535 || w > 65535) return IHIST_ERR_INVALID_ARG;
   if ((unsigned long long)h * (unsigned long long)w >= (1ull << 32)) return IHIST_ERR_INVALID_ARG;
   if (nbins < 1 || nbins > 256) return IHIST_ERR_INVALID_ARG;
@@ -495,8 +486,7 @@ extern "C" int ihist_compute(ihist_plan_t p, const uint8_t *d_in, size_t in_pitc
   return IHIST_OK;
 }
 
-// Eq. 2 launch shared by plans and batches.
-static int launch_query(int H, int W, int B, int layout, int sms, Ctrl *ctrl, const uint32_t *d_hist,
+int ihist::host::launch_query(int H, int W, int B, int layout, int sms, Ctrl *ctrl, const uint32_t *d_hist,
                         const int32_t *d_rects, int n, uint32_t *d_hist_out, void *stream) {
   if (n < 0) return IHIST_ERR_INVALID_ARG;
   if (n == 0) return IHIST_OK;
@@ -612,7 +602,7 @@ extern "C" int ihist_sequence_host(ihist_plan_t p, const uint8_t *h_frames, size
   return IHIST_OK;
 }
 
-static int read_status(Ctrl *ctrl, void *stream, int *device_status) {
+int ihist::host::read_status(Ctrl *ctrl, void *stream, int *device_status) {
   cudaStream_t s = (cudaStream_t)stream;
   int v = 0;
   if (cudaStreamSynchronize(s) != cudaSuccess) return IHIST_ERR_CUDA;
@@ -644,539 +634,3 @@ extern "C" void ihist_destroy(ihist_plan_t p) {
   if (prev != p->device && prev >= 0) cudaSetDevice(prev);
   delete p;
 }
-
-// ---------------------------------------------------------------- batches
-//
-// A batch plan owns `cap` frame slots.  Slot i's carry workspace is sized
-// for the frame it was planned with; ihist_batch_set_io may later bind any
-// n <= cap frames whose tilings fit their slots (same or smaller carries,
-// rows per band and width), so one plan serves a stream of changing
-// batches without allocating.  Every kernel variant (TMA / plain input,
-// 16-byte / scalar output) is prepared at plan time and the launch picks
-// the one the current frames allow.
-
-namespace {
-
-constexpr int kBatchWarps = 16;  // default warps per CTA of the batched kernel
-
-// Tiling of one frame in a batched launch of `warps`-warp CTAs: m chunks
-// per warp (at most max_m) and gpc bin groups per CTA, nchunks * gpc at most
-// max_ncg (the per-CTA carry width the launch's shared memory was sized
-// for), maximising the share of the CTA's warps x m chunk slots that hold
-// columns, smaller m on ties.  Returns false if no tiling fits (the frame
-// is wider than warps x max_m chunks, or its chunks exceed max_ncg).
-bool batch_frame_tiling(int h, int w, int nbins, int layout, int G, int R_req, int max_m, int max_ncg,
-                        int warps, FrameDesc *f) {
-  const int nchunks = (w + kChunk - 1) / kChunk;
-  const int ngroups = (nbins + G - 1) / G;
-  double best = -1.0;
-  int bm = 1, bwpg = nchunks, bgpc = 1;
-  for (int m = 1; m <= max_m; m <<= 1) {
-    const int wpg = (nchunks + m - 1) / m;
-    if (wpg > warps) continue;
-    const int gpc = std::min(std::min(ngroups, warps / wpg), max_ncg / nchunks);
-    if (gpc < 1) continue;
-    const double util = (double)nchunks * gpc / ((double)warps * m);
-    if (util > best + 1e-9) {
-      best = util;
-      bm = m;
-      bwpg = wpg;
-      bgpc = gpc;
-    }
-  }
-  std::memset(f, 0, sizeof(*f));
-  f->H = h;
-  f->W = w;
-  f->B = nbins;
-  f->qmul = nbins;
-  f->layout = layout;
-  f->R = std::min(R_req, h);
-  f->nbands = (h + f->R - 1) / f->R;
-  f->ngroups = ngroups;
-  f->nchunks = nchunks;
-  f->m = bm;
-  f->wpg = bwpg;
-  f->gpc = bgpc;
-  f->ngsets = (ngroups + bgpc - 1) / bgpc;
-  f->nitems = (unsigned int)f->nbands * (unsigned int)f->ngsets;
-  f->fault_skip_band = -1;
-  return best >= 0.0;
-}
-
-size_t frame_nci(const FrameDesc &f) { return (size_t)f.nbands * f.ngroups * f.nchunks; }
-
-bool frame_tma_ok(const ihist_frame_t &fr) {
-  return !((uintptr_t)fr.d_in & 15u) && !(fr.in_pitch & 15u) && fr.w >= kChunk &&
-         fr.in_pitch < (1ull << 40);
-}
-
-bool frame_vec_ok(const ihist_frame_t &fr) {
-  return fr.w % 4 == 0 && !((uintptr_t)fr.d_out & 15u);
-}
-
-}  // namespace
-
-struct ihist_batch_s {
-  int device, sms, cap, n, G, warps, mmax, R_req, R_max, ncg_max, ctas_cap, stage;
-  int fault_skip_band;  // test hook, -1 off
-  int ctas_per_sm[2][2];  // occupancy of each (tma, vec) variant
-  bool tma, vec;          // variant the current frames allow
-  unsigned int timeout_us, total;
-  size_t smem_bytes, ws_bytes;
-  unsigned long long bins_total;
-  void *ws;
-  Ctrl *ctrl;
-  FrameDesc *d_fd;
-  CUtensorMap *d_tm;
-  unsigned int *d_end, *d_bins_end;
-  std::vector<size_t> slot_nci;                       // carry capacity of each slot
-  std::vector<uint32_t *> slot_flags, slot_cnt, slot_left, slot_incl;
-  std::vector<FrameDesc> fd;                          // current frames
-  std::vector<ihist_frame_t> io;
-  FrameDesc *h_fd;           // pinned staging
-  CUtensorMap *h_tm;
-  unsigned int *h_end, *h_bins_end;
-  cudaEvent_t staged;        // last staging copy done
-  cudaEvent_t uploaded, computed;
-  bool launched;
-};
-
-static bool encode_frame_map(const ihist_frame_t &fr, int R, CUtensorMap *map) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return false;
-  cuuint64_t gdim[2] = {(cuuint64_t)fr.w, (cuuint64_t)fr.h};
-  cuuint64_t gstride[1] = {(cuuint64_t)fr.in_pitch};
-  cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)R};
-  cuuint32_t estride[2] = {1u, 1u};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(fr.d_in), gdim, gstride,
-             box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// Tile the given frames into the plan's slots and fill the pinned staging
-// copies (descriptors, tensor maps, item and bin prefix sums).  Nothing is
-// committed to b->fd / b->io unless every frame fits.
-static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames, int n) {
-  if (n < 1 || n > b->cap) return IHIST_ERR_INVALID_ARG;
-  std::vector<FrameDesc> fd(n);
-  bool tma = true, vec = true;
-  unsigned long long total = 0, bsum = 0;
-  for (int i = 0; i < n; ++i) {
-    const ihist_frame_t &fr = frames[i];
-    int rc = validate_shape(fr.h, fr.w, fr.nbins, fr.layout);
-    if (rc != IHIST_OK) return rc;
-    if (!fr.d_in || !fr.d_out || fr.in_pitch < (size_t)fr.w || ((uintptr_t)fr.d_out & 3u) ||
-        fr.in_pitch > (size_t)LLONG_MAX)
-      return IHIST_ERR_INVALID_ARG;
-    FrameDesc &f = fd[i];
-    if (!batch_frame_tiling(fr.h, fr.w, fr.nbins, fr.layout, b->G, b->R_req, b->mmax, b->ncg_max, b->warps,
-                            &f) ||
-        frame_nci(f) > b->slot_nci[i] || f.R > b->R_max || f.nchunks * f.gpc > b->ncg_max ||
-        mmax_for(f.m) > b->mmax)
-      return IHIST_ERR_UNSUPPORTED;  // does not fit the slot planned for it
-    f.in = fr.d_in;
-    f.pitch = (long long)fr.in_pitch;
-    f.out = fr.d_out;
-    f.flags = b->slot_flags[i];
-    f.agg_cnt = b->slot_cnt[i];
-    f.agg_left = b->slot_left[i];
-    f.incl = b->slot_incl[i];
-    f.fault_skip_band = b->fault_skip_band;
-    tma = tma && frame_tma_ok(fr);
-    vec = vec && frame_vec_ok(fr);
-    total += f.nitems;
-    bsum += (unsigned long long)fr.nbins;
-  }
-  if (total >= 0xffffffffull) return IHIST_ERR_UNSUPPORTED;
-  for (int i = 0; i < n; ++i) {
-    if (tma) {
-      if (!encode_frame_map(frames[i], fd[i].R, &b->h_tm[i])) return IHIST_ERR_CUDA;
-    } else {
-      std::memset(&b->h_tm[i], 0, sizeof(CUtensorMap));
-    }
-  }
-  unsigned long long run = 0, brun = 0;
-  for (int i = 0; i < n; ++i) {
-    run += fd[i].nitems;
-    brun += (unsigned long long)frames[i].nbins;
-    b->h_end[i] = (unsigned int)run;
-    b->h_bins_end[i] = (unsigned int)brun;
-    b->h_fd[i] = fd[i];
-  }
-  b->fd.assign(fd.begin(), fd.end());
-  b->io.assign(frames, frames + n);
-  b->n = n;
-  b->tma = tma;
-  b->vec = vec;
-  b->total = (unsigned int)total;
-  b->bins_total = bsum;
-  return IHIST_OK;
-}
-
-static int batch_upload(ihist_batch_s *b, cudaStream_t s) {
-  const int n = b->n;
-  if (cudaMemcpyAsync(b->d_fd, b->h_fd, (size_t)n * sizeof(FrameDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(b->d_tm, b->h_tm, (size_t)n * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(b->d_end, b->h_end, (size_t)n * sizeof(unsigned int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(b->d_bins_end, b->h_bins_end, (size_t)n * sizeof(unsigned int), cudaMemcpyHostToDevice, s) !=
-          cudaSuccess ||
-      cudaEventRecord(b->staged, s) != cudaSuccess)
-    return IHIST_ERR_CUDA;
-  return IHIST_OK;
-}
-
-extern "C" void ihist_batch_destroy(ihist_batch_t b) {
-  if (!b) return;
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != b->device) cudaSetDevice(b->device);
-  if (b->staged) cudaEventSynchronize(b->staged);
-  if (b->staged) cudaEventDestroy(b->staged);
-  if (b->uploaded) cudaEventDestroy(b->uploaded);
-  if (b->computed) cudaEventDestroy(b->computed);
-  if (b->h_fd) cudaFreeHost(b->h_fd);
-  if (b->h_tm) cudaFreeHost(b->h_tm);
-  if (b->h_end) cudaFreeHost(b->h_end);
-  if (b->h_bins_end) cudaFreeHost(b->h_bins_end);
-  if (b->ws) cudaFree(b->ws);
-  if (prev != b->device && prev >= 0) cudaSetDevice(prev);
-  delete b;
-}
-
-extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_tune_t *tune,
-                                ihist_batch_t *out) {
-  if (!frames || n < 1 || !out) return IHIST_ERR_INVALID_ARG;
-  ihist_tune_t t;
-  std::memset(&t, 0, sizeof(t));
-  if (tune) t = *tune;
-  if (t.bins_per_cta == 0) {
-    // larger bin groups when any frame is pixel-major (longer contiguous
-    // pieces per pixel record): 16 when every frame has at least 16 bins and
-    // fits 16 warps x 2 chunks, else 8
-    bool pm = false, wide16 = true;
-    for (int i = 0; i < n; ++i) {
-      pm = pm || frames[i].layout == IHIST_PIXEL_MAJOR;
-      wide16 = wide16 && frames[i].nbins >= 16 && frames[i].w <= kBatchWarps * 2 * kChunk;
-    }
-    t.bins_per_cta = pm ? (wide16 ? 16 : 8) : 4;
-  }
-  if (t.bins_per_cta != 4 && t.bins_per_cta != 8 && t.bins_per_cta != 16) return IHIST_ERR_INVALID_ARG;
-  if (t.rows_per_band < 0 || t.rows_per_band > 255) return IHIST_ERR_INVALID_ARG;
-  if (t.ctas_per_sm < 0 || t.ctas_per_sm > 32) return IHIST_ERR_INVALID_ARG;
-  if (t.warps_per_cta != 0 && t.warps_per_cta != 4 && t.warps_per_cta != 8 && t.warps_per_cta != 16)
-    return IHIST_ERR_INVALID_ARG;
-  for (int i = 0; i < n; ++i) {
-    const int rc = validate_shape(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout);
-    if (rc != IHIST_OK) return rc;
-  }
-  int dev = 0, sms = 0, optin = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return IHIST_ERR_CUDA;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-    return IHIST_ERR_CUDA;
-
-  ihist_batch_s *b = new (std::nothrow) ihist_batch_s();
-  if (!b) return IHIST_ERR_OOM;
-  b->device = dev;
-  b->sms = sms;
-  b->cap = n;
-  b->G = t.bins_per_cta;
-  b->fault_skip_band = t.fault_skip_band >= 1 ? t.fault_skip_band - 1 : -1;
-  // pixel-major frames stage their rows in shared memory
-  b->stage = 0;
-  for (int i = 0; i < n; ++i)
-    if (pm_staged(frames[i].layout, b->G)) b->stage = 1;
-  const int max_m = b->G == 16 ? 2 : 4;  // chunks per warp the instantiations cover
-  b->warps = t.warps_per_cta;
-  if (b->warps == 0) {
-    // 8-warp CTAs (4 per SM overlap their count, look-back and emit phases
-    // better than 2 of 16 warps: 5% faster on 1080p frames), except 16 for
-    // staged pixel-major rows in 8-bin groups (64 pixel-major 1080p frames:
-    // 8 bins 10.5 ms with 16 warps against 11.7 with 8; 16 bins 8.2 ms with
-    // 8 warps against 8.5 with 16) and for frames wider than 8 warps x
-    // max_m chunks
-    b->warps = (b->stage && b->G != 16) ? kBatchWarps : 8;
-    for (int i = 0; i < n; ++i)
-      if (frames[i].w > 8 * max_m * kChunk) b->warps = kBatchWarps;
-  }
-  b->timeout_us = t.timeout_us ? t.timeout_us : kDefaultTimeoutUs;
-  // every kernel variant the batch may launch may use the opt-in shared memory
-  for (int mm = 1; mm <= max_m; mm <<= 1)
-    for (int tma = 0; tma < 2; ++tma)
-      for (int vec = 0; vec < 2; ++vec) {
-        BatchFn fn = batch_fn(b->G, mm, tma != 0, vec != 0);
-        cudaFuncAttributes a;
-        if (!fn || cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
-          cudaGetLastError();
-          delete b;
-          return fn ? IHIST_ERR_CUDA : IHIST_ERR_UNSUPPORTED;
-        }
-        const size_t dyn_max = (size_t)optin > a.sharedSizeBytes ? (size_t)optin - a.sharedSizeBytes : 0;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max) != cudaSuccess) {
-          cudaGetLastError();
-          delete b;
-          return IHIST_ERR_CUDA;
-        }
-      }
-  // default rows per band: the largest R (at most 64) at which the kernel
-  // still keeps 32 warps per SM (each warp stages R rows of input and row
-  // carries in shared memory), as the occupancy calculator reports it
-  // every frame must have a tiling in CTAs of this many warps
-  for (int i = 0; i < n; ++i) {
-    FrameDesc f;
-    if (!batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, 8, max_m,
-                            INT_MAX, b->warps, &f)) {
-      delete b;
-      return IHIST_ERR_UNSUPPORTED;
-    }
-  }
-  b->R_req = t.rows_per_band;
-  if (b->R_req == 0) {
-    // the largest R (at most 64) that keeps the CTAs per SM that the
-    // smallest bands allow (registers permitting: 4 of 8 warps or 2 of 16
-    // warps with 4 or 8 bins per CTA, 1 with 16)
-    auto occ_at = [&](int r) {
-      int rmax = 1, ncg = 1, mm = 1;
-      for (int i = 0; i < n; ++i) {
-        FrameDesc f;
-        batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, r, max_m, INT_MAX,
-                           b->warps, &f);
-        rmax = std::max(rmax, f.R);
-        ncg = std::max(ncg, f.nchunks * f.gpc);
-        mm = std::max(mm, f.m);
-      }
-      int occ = 0;
-      const size_t smem = smem_layout(b->warps, rmax, b->G, ncg, b->stage != 0).bytes;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_fn(b->G, mmax_for(mm), true, true),
-                                                        b->warps * 32, smem) != cudaSuccess) {
-        cudaGetLastError();
-        occ = 0;
-      }
-      return occ;
-    };
-    const int target = std::max(1, occ_at(8));
-    b->R_req = 8;
-    for (int r = 64; r >= 8; --r) {
-      if (occ_at(r) >= target) {
-        b->R_req = r;
-        break;
-      }
-    }
-  }
-  // slot capacities from the planned frames
-  std::vector<FrameDesc> plan_fd(n);
-  int mm = 1;
-  size_t nci_total = 0;
-  for (int i = 0; i < n; ++i) {
-    batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, b->R_req, max_m,
-                       INT_MAX, b->warps, &plan_fd[i]);
-    mm = std::max(mm, plan_fd[i].m);
-    b->R_max = std::max(b->R_max, plan_fd[i].R);
-    b->ncg_max = std::max(b->ncg_max, plan_fd[i].nchunks * plan_fd[i].gpc);
-    b->slot_nci.push_back(frame_nci(plan_fd[i]));
-    nci_total += frame_nci(plan_fd[i]);
-  }
-  b->mmax = mmax_for(mm);
-  b->smem_bytes = smem_layout(b->warps, b->R_max, b->G, b->ncg_max, b->stage != 0).bytes;
-  for (int tma = 0; tma < 2; ++tma)
-    for (int vec = 0; vec < 2; ++vec) {
-      BatchFn fn = batch_fn(b->G, b->mmax, tma != 0, vec != 0);
-      cudaFuncAttributes a;
-      if (!fn || cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
-        cudaGetLastError();
-        delete b;
-        return fn ? IHIST_ERR_CUDA : IHIST_ERR_UNSUPPORTED;
-      }
-      const size_t dyn_max = (size_t)optin > a.sharedSizeBytes ? (size_t)optin - a.sharedSizeBytes : 0;
-      int occ = 0;
-      if (b->smem_bytes > dyn_max ||
-          cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max) != cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, b->warps * 32, b->smem_bytes) != cudaSuccess ||
-          occ < 1) {
-        cudaGetLastError();
-        delete b;
-        return IHIST_ERR_UNSUPPORTED;
-      }
-      b->ctas_per_sm[tma][vec] = t.ctas_per_sm > 0 ? std::min(t.ctas_per_sm, occ) : occ;
-    }
-
-  // workspace: control block and flags (cleared), descriptor arrays
-  // (written only by copies), then each slot's carries
-  size_t off = 0;
-  const size_t o_ctrl = off;
-  off = align_up(off + sizeof(Ctrl), 256);
-  const size_t o_flags = off;
-  off = align_up(off + nci_total * sizeof(uint32_t), 256);
-  const size_t zero_end = off;
-  const size_t o_fd = off;
-  off = align_up(off + (size_t)n * sizeof(FrameDesc), 256);
-  const size_t o_tm = off;
-  off = align_up(off + (size_t)n * sizeof(CUtensorMap), 256);
-  const size_t o_end = off;
-  off = align_up(off + (size_t)n * sizeof(unsigned int), 256);
-  const size_t o_bend = off;
-  off = align_up(off + (size_t)n * sizeof(unsigned int), 256);
-  const size_t o_carry = off;
-  for (int i = 0; i < n; ++i) {
-    const size_t nci = b->slot_nci[i];
-    off = align_up(off + nci * kChunk * (b->G / 4) * 4, 256);
-    off = align_up(off + nci * b->G * 4, 256);
-    off = align_up(off + nci * b->G * kChunk * 4, 256);
-  }
-  b->ws_bytes = off;
-  if (cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess ||
-      cudaMallocHost((void **)&b->h_fd, (size_t)n * sizeof(FrameDesc)) != cudaSuccess ||
-      cudaMallocHost((void **)&b->h_tm, (size_t)n * sizeof(CUtensorMap)) != cudaSuccess ||
-      cudaMallocHost((void **)&b->h_end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
-      cudaMallocHost((void **)&b->h_bins_end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->computed, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    ihist_batch_destroy(b);
-    return IHIST_ERR_OOM;
-  }
-  char *base = static_cast<char *>(b->ws);
-  b->ctrl = reinterpret_cast<Ctrl *>(base + o_ctrl);
-  b->d_fd = reinterpret_cast<FrameDesc *>(base + o_fd);
-  b->d_tm = reinterpret_cast<CUtensorMap *>(base + o_tm);
-  b->d_end = reinterpret_cast<unsigned int *>(base + o_end);
-  b->d_bins_end = reinterpret_cast<unsigned int *>(base + o_bend);
-  size_t fo = o_flags, co = o_carry;
-  for (int i = 0; i < n; ++i) {
-    const size_t nci = b->slot_nci[i];
-    b->slot_flags.push_back(reinterpret_cast<uint32_t *>(base + fo));
-    fo += nci * sizeof(uint32_t);
-    b->slot_cnt.push_back(reinterpret_cast<uint32_t *>(base + co));
-    co = align_up(co + nci * kChunk * (b->G / 4) * 4, 256);
-    b->slot_left.push_back(reinterpret_cast<uint32_t *>(base + co));
-    co = align_up(co + nci * b->G * 4, 256);
-    b->slot_incl.push_back(reinterpret_cast<uint32_t *>(base + co));
-    co = align_up(co + nci * b->G * kChunk * 4, 256);
-  }
-  int rc = batch_bind(b, frames, n);
-  if (rc != IHIST_OK) {
-    ihist_batch_destroy(b);
-    return rc;
-  }
-  // clear the control block and the flags only; the descriptor arrays are
-  // written once per binding by the copies
-  if (cudaMemset(b->ws, 0, zero_end) != cudaSuccess || batch_upload(b, 0) != IHIST_OK ||
-      cudaDeviceSynchronize() != cudaSuccess) {
-    cudaGetLastError();
-    ihist_batch_destroy(b);
-    return IHIST_ERR_CUDA;
-  }
-  (void)o_ctrl;
-  *out = b;
-  return IHIST_OK;
-}
-
-static int check_batch_device(const ihist_batch_s *b) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return IHIST_ERR_CUDA;
-  return dev == b->device ? IHIST_OK : IHIST_ERR_INVALID_ARG;
-}
-
-extern "C" int ihist_batch_get_tune(ihist_batch_t b, ihist_tune_t *out) {
-  if (!b || !out) return IHIST_ERR_INVALID_ARG;
-  std::memset(out, 0, sizeof(*out));
-  out->rows_per_band = b->R_req;
-  out->bins_per_cta = b->G;
-  out->chunks_per_warp = b->mmax;
-  out->ctas_per_sm = b->ctas_per_sm[1][1];
-  out->timeout_us = b->timeout_us;
-  out->fault_skip_band = b->fault_skip_band + 1;  // 0 = off
-  out->groups_per_cta = 0;  // chosen per frame
-  out->warps_per_cta = b->warps;
-  return IHIST_OK;
-}
-
-extern "C" int ihist_batch_set_io(ihist_batch_t b, const ihist_frame_t *frames, int n, void *stream) {
-  if (!b || !frames) return IHIST_ERR_INVALID_ARG;
-  int rc = check_batch_device(b);
-  if (rc != IHIST_OK) return rc;
-  // the staging buffers may still feed the previous copy
-  if (cudaEventSynchronize(b->staged) != cudaSuccess) return IHIST_ERR_CUDA;
-  rc = batch_bind(b, frames, n);
-  if (rc != IHIST_OK) return rc;
-  return batch_upload(b, (cudaStream_t)stream);
-}
-
-extern "C" int ihist_batch_compute(ihist_batch_t b, void *stream) {
-  if (!b) return IHIST_ERR_INVALID_ARG;
-  int rc = check_batch_device(b);
-  if (rc != IHIST_OK) return rc;
-  BatchFn fn = batch_fn(b->G, b->mmax, b->tma, b->vec);
-  const int cps = b->ctas_per_sm[b->tma ? 1 : 0][b->vec ? 1 : 0];
-  const unsigned int grid = std::min<unsigned int>(b->total, (unsigned int)(cps * b->sms));
-  const unsigned long long timeout_ns = (unsigned long long)b->timeout_us * 1000ull;
-  fn<<<grid, b->warps * 32, b->smem_bytes, (cudaStream_t)stream>>>(
-      b->d_fd, b->d_tm, b->d_end, b->n, b->R_max, b->ncg_max, b->stage, b->ctrl, timeout_ns);
-  if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
-  if (cudaEventRecord(b->computed, (cudaStream_t)stream) != cudaSuccess) return IHIST_ERR_CUDA;
-  b->launched = true;
-  return IHIST_OK;
-}
-
-extern "C" int ihist_batch_upload_compute(ihist_batch_t b, const uint8_t *const *h_frames, void *stream,
-                                          void *copy_stream) {
-  if (!b || !h_frames) return IHIST_ERR_INVALID_ARG;
-  for (int i = 0; i < b->n; ++i)
-    if (!h_frames[i]) return IHIST_ERR_INVALID_ARG;
-  int rc = check_batch_device(b);
-  if (rc != IHIST_OK) return rc;
-  cudaStream_t s = (cudaStream_t)stream, cs = (cudaStream_t)copy_stream;
-  // inputs are overwritten only after the previous compute of this batch read them
-  if (b->launched && cudaStreamWaitEvent(cs, b->computed, 0) != cudaSuccess) return IHIST_ERR_CUDA;
-  for (int i = 0; i < b->n; ++i) {
-    const ihist_frame_t &fr = b->io[i];
-    if (cudaMemcpy2DAsync(const_cast<uint8_t *>(fr.d_in), fr.in_pitch, h_frames[i], (size_t)fr.w,
-                          (size_t)fr.w, (size_t)fr.h, cudaMemcpyHostToDevice, cs) != cudaSuccess)
-      return IHIST_ERR_CUDA;
-  }
-  if (cudaEventRecord(b->uploaded, cs) != cudaSuccess ||
-      cudaStreamWaitEvent(s, b->uploaded, 0) != cudaSuccess)
-    return IHIST_ERR_CUDA;
-  return ihist_batch_compute(b, stream);
-}
-
-extern "C" int ihist_batch_query_all(ihist_batch_t b, const int32_t *d_rects, int n, uint32_t *d_out,
-                                     void *stream) {
-  if (!b || n < 0) return IHIST_ERR_INVALID_ARG;
-  if (n == 0) return IHIST_OK;
-  if (!d_rects || !d_out || ((uintptr_t)d_rects & 3u) || ((uintptr_t)d_out & 3u))
-    return IHIST_ERR_INVALID_ARG;
-  int rc = check_batch_device(b);
-  if (rc != IHIST_OK) return rc;
-  if (b->bins_total * (unsigned long long)n >= (1ull << 40)) return IHIST_ERR_UNSUPPORTED;
-  const unsigned long long total = b->bins_total * (unsigned long long)n;
-  const unsigned int threads = 256;
-  const unsigned long long want = (total + threads - 1) / threads;
-  const unsigned int grid = (unsigned int)std::min<unsigned long long>(want, (unsigned long long)b->sms * 16ull);
-  query_batch_kernel<FrameDesc><<<grid, threads, 0, (cudaStream_t)stream>>>(
-      b->d_fd, b->d_bins_end, b->n, d_rects, (unsigned int)n, total, d_out, b->ctrl);
-  if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
-  return IHIST_OK;
-}
-
-extern "C" int ihist_batch_query(ihist_batch_t b, int frame, const uint32_t *d_hist,
-                                 const int32_t *d_rects, int n, uint32_t *d_hist_out, void *stream) {
-  if (!b || frame < 0 || frame >= b->n || n < 0) return IHIST_ERR_INVALID_ARG;
-  if (n == 0) return IHIST_OK;
-  int rc = check_batch_device(b);
-  if (rc != IHIST_OK) return rc;
-  const FrameDesc &f = b->fd[frame];
-  return launch_query(f.H, f.W, f.B, f.layout, b->sms, b->ctrl, d_hist, d_rects, n, d_hist_out, stream);
-}
-
-extern "C" int ihist_batch_status(ihist_batch_t b, void *stream, int *device_status) {
-  if (!b || !device_status) return IHIST_ERR_INVALID_ARG;
-  int rc = check_batch_device(b);
-  if (rc != IHIST_OK) return rc;
-  return read_status(b->ctrl, stream, device_status);
-}
-
-extern "C" size_t ihist_batch_workspace_bytes(ihist_batch_t b) { return b ? b->ws_bytes : 0; }
-
-extern "C" unsigned int ihist_batch_items(ihist_batch_t b) { return b ? b->total : 0u; }

@@ -28,9 +28,11 @@
 #include <mutex>
 
 #include "ihist.h"
+#include "ihist_host.h"
 #include "ihist_kernels.h"
 
 using namespace ihist;
+using namespace ihist::host;
 
 namespace {
 
@@ -52,10 +54,6 @@ struct DeviceSetup {
 
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
-
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-int mmax_for(int m) { return m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : 8; }
 
 // Once per device, with that device current: the device address of the
 // scratch array (the host-side name of a __device__ array is not a device
@@ -97,21 +95,6 @@ int setup_device(int dev, DeviceSetup **out) {
   }
   *out = &s;
   return IHIST_OK;
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }();
-  return fn;
 }
 
 // Scratch bytes for nci (band, bin group, chunk) carry slots.
@@ -198,7 +181,7 @@ extern "C" int ihist_compute_noalloc(int h, int w, int nbins, int layout, const 
   CUtensorMap tmap;
   std::memset(&tmap, 0, sizeof(tmap));
   if (tma) {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     cuuint64_t gdim[2] = {(cuuint64_t)w, (cuuint64_t)h};
     cuuint64_t gstride[1] = {(cuuint64_t)in_pitch};
     cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)R};
