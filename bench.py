@@ -255,11 +255,11 @@ def serving_report(seconds: float) -> dict:
 
     keep = ("completed", "rejected", "p50_ms", "p99_ms", "per_s")
     out = {"workload": "Poisson arrivals for %.1f s: frames at 2000/s (320x240..1920x1080, 16-64 bins), "
-                       "queries of 10,000 rects at 200/s against a random resident histogram; "
-                       "40 GB budget, LRU eviction" % seconds}
+                       "queries of 10,000 rects at 200/s and searches for a 64x64 patch (stride 8) at 50/s "
+                       "against a random resident histogram; 40 GB budget, LRU eviction" % seconds}
     for mode in ("batched", "plain"):
         rep = serve.serve(mode=mode, duration_s=seconds)
-        out[mode] = {k: {f: rep[k][f] for f in keep} for k in ("frame", "query")}
+        out[mode] = {k: {f: rep[k][f] for f in keep} for k in ("frame", "query", "search")}
         out[mode]["evicted"] = rep["evicted"]
     for mode in ("batched", "plain"):
         rep = serve.serve(mode=mode, duration_s=seconds / 4, saturate=True)

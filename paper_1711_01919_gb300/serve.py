@@ -12,6 +12,10 @@ Requests arrive over time (Sec. 4.4's image sequences, served):
   resident frames whose histogram is complete when the query is admitted
   (seeded, uniform) and holds it until the query is answered; the rows are
   copied back to the host.
+* ``SearchRequest``  a patch of a resident frame to find again: its region
+  histogram becomes the target of a sliding-window search over the frame,
+  and the best window (score, i, j) comes back (tracking, Sec. 1).  Targets
+  are chosen and held like a query's.
 
 The loop is continuous batching, not a queue: every iteration it admits
 what has arrived and fits, puts all admitted frames that are not yet
@@ -66,9 +70,26 @@ class QueryRequest:
 
 
 @dataclasses.dataclass
+class SearchRequest:
+    """Where in a resident frame does this patch's histogram fit best?  The
+    target is the histogram of the win_h x win_w patch at (y, x) of the
+    chosen frame (a region query); the answer is the best window of the
+    sliding-window search over that frame (score, i, j) -- the tracking use
+    of the integral histogram (Sec. 1)."""
+    rid: int
+    t_arrival: float
+    y: int
+    x: int
+    win_h: int
+    win_w: int
+    stride: int
+    target: int = -1          # frame rid, chosen at admission
+
+
+@dataclasses.dataclass
 class Done:
     rid: int
-    kind: str                 # "frame" or "query"
+    kind: str                 # "frame", "query" or "search"
     t_arrival: float
     t_done: float
     status: str = "ok"        # ok | rejected
@@ -166,6 +187,10 @@ class FakeExecutor:
         self.launches.append(("query", q.rid, q.target))
         return {"t": t + self.query_latency, "result": ("rows", q.rid, payload)}
 
+    def launch_search(self, q, payload, t):
+        self.launches.append(("search", q.rid, q.target))
+        return {"t": t + self.query_latency, "result": ("best", q.rid, payload)}
+
     def poll(self, handle, t):
         return t >= handle["t"]
 
@@ -194,7 +219,7 @@ class Server:
         self.results = {}
         self.keep_results = keep_results  # copy each query's rows out of the executor's reusable buffers
         self.batch_sizes = collections.Counter()
-        self.host_ms = {"frames": [], "query": []}  # host time spent issuing each launch
+        self.host_ms = {"frames": [], "query": [], "search": []}  # host time spent issuing each launch
 
     def run(self, requests, clock, max_wall: float = 600.0):
         """Serve `requests` (sorted by t_arrival).  clock() returns seconds since
@@ -230,7 +255,7 @@ class Server:
                 else:
                     live = self.store.ready_ids()
                     if not live:
-                        self.done.append(Done(r.rid, "query", r.t_arrival, t, "rejected"))
+                        self.done.append(Done(r.rid, _kind(r), r.t_arrival, t, "rejected"))
                         continue
                     r.target = int(live[int(self.rng.integers(len(live)))])
                     self.store.pin(r.target)
@@ -252,10 +277,11 @@ class Server:
                 q = waiting_queries.popleft()
                 if self.store.ready(q.target):
                     t_call = clock()
-                    h = self.ex.launch_query(q, self.store.payload(q.target), t)
+                    launch = self.ex.launch_search if isinstance(q, SearchRequest) else self.ex.launch_query
+                    h = launch(q, self.store.payload(q.target), t)
                     h["t_launch"] = clock()
-                    self.host_ms["query"].append(1e3 * (h["t_launch"] - t_call))
-                    inflight.append((h, "query", q))
+                    self.host_ms[_kind(q)].append(1e3 * (h["t_launch"] - t_call))
+                    inflight.append((h, _kind(q), q))
                 else:
                     waiting_queries.append(q)
             # 4. one batched launch of everything admitted (continuous batching)
@@ -286,7 +312,7 @@ class Server:
                         if self.keep_results:
                             r = h.get("result")
                             self.results[obj.rid] = r.clone() if hasattr(r, "clone") else r
-                        self.done.append(Done(obj.rid, "query", obj.t_arrival, td, target=obj.target,
+                        self.done.append(Done(obj.rid, kind, obj.t_arrival, td, target=obj.target,
                                               t_launch=h["t_launch"]))
                 else:
                     still.append((h, kind, obj))
@@ -297,7 +323,7 @@ class Server:
         out = {"mode": self.mode, "evicted": self.store.evicted,
                "launch_sizes": {str(k): v for k, v in sorted(self.batch_sizes.items())},
                "host_issue_p50_ms": {k: float(np.percentile(v, 50)) if v else None for k, v in self.host_ms.items()}}
-        for kind in ("frame", "query"):
+        for kind in ("frame", "query", "search"):
             ok = [d for d in self.done if d.kind == kind and d.status == "ok"]
             lat = np.array([d.t_done - d.t_arrival for d in ok]) * 1e3
             wait = np.array([d.t_launch - d.t_arrival for d in ok]) * 1e3  # host: arrival -> launched
@@ -314,13 +340,29 @@ class Server:
         return out
 
 
+def _kind(r) -> str:
+    return "search" if isinstance(r, SearchRequest) else "query"
+
+
+def decode_best(v: int, nx: int):
+    """(score, i, j) of a packed best window (see ihist_window_search), or None."""
+    v &= 0xffffffffffffffff
+    if v == 0:
+        return None
+    idx = 0xffffffff - (v & 0xffffffff)
+    return v >> 32, idx // nx, idx % nx
+
+
 # ----------------------------------------------------------------- workload
 
 def serving_workload(seed: int, duration_s: float, frame_rate: float = 2000.0, query_rate: float = 200.0,
-                     rects_per_query: int = 10000, frame_pool=None):
-    """Poisson frame arrivals (mix of the uneven batch) and Poisson query
-    arrivals with `rects_per_query` random rectangles each.  frame_pool:
-    optional {(h, w): [frames]} of host frames to cycle through."""
+                     rects_per_query: int = 10000, frame_pool=None, search_rate: float = 0.0,
+                     search_win=(64, 64), search_stride: int = 8):
+    """Poisson frame arrivals (mix of the uneven batch), Poisson query
+    arrivals with `rects_per_query` random rectangles each, and Poisson
+    search arrivals (a search_win patch of the chosen frame, searched for on
+    a search_stride grid).  frame_pool: optional {(h, w): [frames]} of host
+    frames to cycle through."""
     ft = synth.poisson_arrivals(seed, frame_rate, duration_s)
     qt = synth.poisson_arrivals(seed + 1, query_rate, duration_s)
     specs = synth.uneven_batch_specs(seed + 2, len(ft))
@@ -337,6 +379,16 @@ def serving_workload(seed: int, duration_s: float, frame_rate: float = 2000.0, q
     for j, t in enumerate(qt):
         # rectangles in the smallest resolution of the mix, valid in every frame
         reqs.append(QueryRequest(n0 + j, float(t), synth.rects(seed + 10 + j, rects_per_query, 240, 320)))
+    if search_rate > 0:
+        st = synth.poisson_arrivals(seed + 3, search_rate, duration_s)
+        wh, ww = search_win
+        # patch corners on the stride grid inside the smallest resolution of the mix
+        corners = synth.splitmix64(seed + 4, 2 * len(st)).reshape(-1, 2)
+        n1 = len(reqs)
+        for k, t in enumerate(st):
+            y = int(corners[k, 0] % np.uint64((240 - wh) // search_stride + 1)) * search_stride
+            x = int(corners[k, 1] % np.uint64((320 - ww) // search_stride + 1)) * search_stride
+            reqs.append(SearchRequest(n1 + k, float(t), y, x, wh, ww, search_stride))
     reqs.sort(key=lambda r: r.t_arrival)
     return reqs
 
@@ -401,6 +453,8 @@ class GpuExecutor:
                 "d_rects": torch.empty((max_rects, 4), dtype=torch.int32, device="cuda"),
                 "d_out": torch.empty((max_rects * 256,), dtype=torch.int32, device="cuda"),
                 "h_out": torch.empty((max_rects * 256,), dtype=torch.int32, pin_memory=True),
+                "d_best": torch.zeros((1,), dtype=torch.int64, device="cuda"),
+                "h_best": torch.zeros((1,), dtype=torch.int64, pin_memory=True),
                 "free": None,  # event: the slot's last rows have reached the host
             })
         self.next_qslot = 0
@@ -494,6 +548,39 @@ class GpuExecutor:
             if self.trace:
                 self.torch.cuda.nvtx.range_pop()
 
+    def launch_search(self, q, payload, t):
+        if self.trace:
+            self.torch.cuda.nvtx.range_push("ihist search %dx%d/%d" % (q.win_h, q.win_w, q.stride))
+        try:
+            return self._launch_search(q, payload, t)
+        finally:
+            if self.trace:
+                self.torch.cuda.nvtx.range_pop()
+
+    def _launch_search(self, q, payload, t):
+        # the target is the patch's own region histogram (Eq. 2), then the
+        # search keeps only the best window; 8 bytes come back
+        torch, ih = self.torch, self.ih
+        hist, h, w, b = payload
+        slot = self.qslots[self.next_qslot]
+        self.next_qslot = (self.next_qslot + 1) % len(self.qslots)
+        if slot["free"] is not None:
+            slot["free"].synchronize()
+        slot["h_rects"].numpy()[0] = (q.x, q.y, q.x + q.win_w - 1, q.y + q.win_h - 1)
+        qs = self.qstream.cuda_stream
+        plan = self._plan(h, w, b)
+        with torch.cuda.stream(self.qstream):
+            slot["d_rects"][:1].copy_(slot["h_rects"][:1], non_blocking=True)
+            ih.ihist_query(plan.handle, hist.data_ptr(), slot["d_rects"].data_ptr(), 1, slot["d_out"].data_ptr(), qs)
+            ih.ihist_window_search(plan.handle, hist.data_ptr(), slot["d_out"].data_ptr(), q.win_h, q.win_w, q.stride,
+                                   0, slot["d_best"].data_ptr(), qs)
+            slot["h_best"].copy_(slot["d_best"], non_blocking=True)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(self.qstream)
+        slot["free"] = ev
+        hist.record_stream(self.qstream)
+        return {"ev": ev, "result": slot["h_best"], "nx": ih.window_grid(h, w, q.win_h, q.win_w, q.stride)[1]}
+
     def _launch_query(self, q, payload, t):
         # the server launches a query only once its histogram is complete,
         # and keeps the histogram resident until the query is done
@@ -536,7 +623,7 @@ class GpuExecutor:
 
 
 def serve(mode="batched", duration_s=2.0, budget_gb=40.0, seed=None, frame_rate=2000.0, query_rate=200.0,
-          rects_per_query=10000, pool_per_shape=8, saturate=False, trace=False):
+          rects_per_query=10000, pool_per_shape=8, saturate=False, trace=False, search_rate=50.0):
     """Run the serving workload on the GPU; returns the server's report."""
     import torch
     seed = synth.workload_seed(4) if seed is None else seed
@@ -544,7 +631,7 @@ def serve(mode="batched", duration_s=2.0, budget_gb=40.0, seed=None, frame_rate=
     for (w, h) in synth.BATCH_RESOLUTIONS:
         pool[(h, w)] = [torch.from_numpy(synth.uniform_frame(seed + 100 * k + w, h, w)).pin_memory()
                         for k in range(pool_per_shape)]
-    reqs = serving_workload(seed, duration_s, frame_rate, query_rate, rects_per_query, pool)
+    reqs = serving_workload(seed, duration_s, frame_rate, query_rate, rects_per_query, pool, search_rate)
     if saturate:
         # the same requests, arriving 1000 times faster than the server can take them
         for r in reqs:

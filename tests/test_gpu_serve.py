@@ -23,7 +23,7 @@ def run_server(mode, duration=0.04, budget_gb=40.0, saturate=False):
     pool = {}
     for (w, h) in synth.BATCH_RESOLUTIONS:
         pool[(h, w)] = [torch.from_numpy(synth.uniform_frame(seed + 7 * k + w, h, w)).pin_memory() for k in range(3)]
-    reqs = serve.serving_workload(seed, duration, 2000.0, 200.0, 500, pool)
+    reqs = serve.serving_workload(seed, duration, 2000.0, 200.0, 500, pool, search_rate=300.0)
     if saturate:
         for r in reqs:
             r.t_arrival = 0.0
@@ -56,6 +56,16 @@ def check_alone(srv, reqs):
             d_rects = torch.from_numpy(np.ascontiguousarray(q.rects)).cuda()
             ref = plans[(r.h, r.w, r.nbins)].query(alone[q.target], d_rects)
             assert torch.equal(srv.results[q.rid], ref.cpu()), "query %d differs" % q.rid
+            nq += 1
+        if isinstance(q, serve.SearchRequest) and q.rid in srv.results and q.target in alone:
+            r = frames[q.target]
+            plan = plans[(r.h, r.w, r.nbins)]
+            rect = torch.tensor([[q.x, q.y, q.x + q.win_w - 1, q.y + q.win_h - 1]], dtype=torch.int32, device="cuda")
+            target = plan.query(alone[q.target], rect)[0].contiguous()
+            ref = plan.window_best(alone[q.target], target, q.win_h, q.win_w, q.stride)
+            nx = ihist.window_grid(r.h, r.w, q.win_h, q.win_w, q.stride)[1]
+            assert serve.decode_best(int(srv.results[q.rid].item()), nx) == ref, "search %d differs" % q.rid
+            assert ref[0] == q.win_h * q.win_w  # the patch itself matches fully
             nq += 1
     for p in plans.values():
         p.close()

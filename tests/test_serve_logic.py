@@ -114,3 +114,28 @@ def test_query_targets_only_finished_histograms():
     done = {d.rid: d for d in srv.run(reqs, Clock(1e-4))}
     assert done[10].status == "rejected"
     assert done[11].status == "ok" and done[11].target == 0
+
+
+def test_search_requests_are_held_and_answered_like_queries():
+    nb = serve.hist_bytes(10, 10, 4)
+    ex = serve.FakeExecutor(frame_latency=1e-4, query_latency=2e-3)
+    srv = serve.Server(ex, budget_bytes=10 * nb, seed=0)
+    reqs = frames(2) + [serve.SearchRequest(50, 1e-3, 0, 0, 4, 4, 2)]
+    done = {d.rid: d for d in srv.run(reqs, Clock(1e-4))}
+    assert done[50].kind == "search" and done[50].status == "ok" and done[50].target in (0, 1)
+    assert ("search", 50, done[50].target) in ex.launches
+    assert srv.report(1.0)["search"]["completed"] == 1
+
+
+def test_search_workload_patches_sit_on_the_grid_inside_the_smallest_frame():
+    reqs = serve.serving_workload(3, 0.5, rects_per_query=4, search_rate=100.0, search_win=(64, 64), search_stride=8)
+    ss = [r for r in reqs if isinstance(r, serve.SearchRequest)]
+    assert 20 < len(ss) < 90
+    for r in ss:
+        assert r.y % 8 == 0 and r.x % 8 == 0 and r.y + 64 <= 240 and r.x + 64 <= 320
+
+
+def test_decode_best():
+    assert serve.decode_best(0, 10) is None
+    v = (4096 << 32) | (0xffffffff - 23)
+    assert serve.decode_best(v, 10) == (4096, 2, 3)
