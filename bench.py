@@ -304,18 +304,19 @@ def configs_report(stream, peak: float) -> dict:
     ou = [torch.empty((b, h, w), dtype=torch.int32, device="cuda") for _ in range(8)]
     rects = torch.from_numpy(synth.rects(seed + 1, 1000, h, w)).cuda()
     q = torch.empty((1000, b), dtype=torch.int32, device="cuda")
-    with ihist.Plan(h, w, b) as plan:
-        def vga():
-            for i in range(64):
-                ihist.ihist_compute(plan.handle, fr[i % 8].data_ptr(), w, ou[i % 8].data_ptr(), s)
-                ihist.ihist_query(plan.handle, ou[i % 8].data_ptr(), rects.data_ptr(), 1000, q.data_ptr(), s)
-        ms = _median_ms(vga, stream)
-        if plan.status() != ihist.IHIST_OK:
-            raise SystemExit("device status error in the 640x480 run")
-        byts = 64 * (h * w * b * 4 + h * w)
-        rep["vga_640x480_b32_1000q"] = {"frames_per_s": 64e3 / ms, "us_per_frame": ms * 1e3 / 64,
-                                        "gbs": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak,
-                                        "form": "ihist_compute + ihist_query per frame"}
+    byts = 64 * (h * w * b * 4 + h * w)
+    for label, tune in (("vga_640x480_b32_1000q", None), ("vga_640x480_b32_1000q_overlapped", {"overlap": 1})):
+        with ihist.Plan(h, w, b, tune=tune) as plan:
+            def vga():
+                for i in range(64):
+                    ihist.ihist_compute(plan.handle, fr[i % 8].data_ptr(), w, ou[i % 8].data_ptr(), s)
+                    ihist.ihist_query(plan.handle, ou[i % 8].data_ptr(), rects.data_ptr(), 1000, q.data_ptr(), s)
+            ms = _median_ms(vga, stream)
+            if plan.status() != ihist.IHIST_OK:
+                raise SystemExit("device status error in the 640x480 run")
+            rep[label] = {"frames_per_s": 64e3 / ms, "us_per_frame": ms * 1e3 / 64,
+                          "gbs": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak,
+                          "form": "ihist_compute + ihist_query per frame" + (", overlap=1" if tune else "")}
     del fr, ou, rects, q
     # 256 uneven frames in one launch
     specs = synth.uneven_batch_specs(synth.workload_seed(3), 256)
@@ -584,29 +585,37 @@ def main():
         raise SystemExit("device status error during the timed region")
     resident_query = d_query.view(NFRAMES, NRECTS, NBINS)[NFRAMES - 1].cpu()
 
-    # ---- plain per-frame launches (same frames, same outputs) ----
-    plan = ihist.Plan(H, W, NBINS, layout)
+    # ---- plain per-frame launches (same frames, same outputs); then the
+    # same with overlapped launches (no kernel in the step writes a frame) ----
     pf_steps = max(3, min(args.steps, 20))
 
-    def plain_step():
-        for f in range(NFRAMES):
-            ihist.ihist_compute(plan.handle, d_frames[f].data_ptr(), W, outs[f].data_ptr(), s)
-            ihist.ihist_query(plan.handle, outs[f].data_ptr(), rp, NRECTS, d_query[f * NRECTS * NBINS:].data_ptr(), s)
+    def time_plain(plan):
+        def plain_step():
+            for f in range(NFRAMES):
+                ihist.ihist_compute(plan.handle, d_frames[f].data_ptr(), W, outs[f].data_ptr(), s)
+                ihist.ihist_query(plan.handle, outs[f].data_ptr(), rp, NRECTS,
+                                  d_query[f * NRECTS * NBINS:].data_ptr(), s)
 
-    for _ in range(2):
-        plain_step()
-    p_start, p_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    p_start.record(stream)
-    for _ in range(pf_steps):
-        plain_step()
-    p_end.record(stream)
-    torch.cuda.synchronize()
-    plain_ms = p_start.elapsed_time(p_end)
-    if plan.status() != ihist.IHIST_OK:
-        raise SystemExit("device status error in the per-frame run")
-    if not torch.equal(d_query.view(NFRAMES, NRECTS, NBINS)[NFRAMES - 1].cpu(), resident_query):
-        raise SystemExit("per-frame and batched query results differ")
+        d_query.fill_(-1)
+        for _ in range(2):
+            plain_step()
+        p_start, p_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        p_start.record(stream)
+        for _ in range(pf_steps):
+            plain_step()
+        p_end.record(stream)
+        torch.cuda.synchronize()
+        if plan.status() != ihist.IHIST_OK:
+            raise SystemExit("device status error in the per-frame run")
+        if not torch.equal(d_query.view(NFRAMES, NRECTS, NBINS)[NFRAMES - 1].cpu(), resident_query):
+            raise SystemExit("per-frame and batched query results differ")
+        return p_start.elapsed_time(p_end)
+
+    plan = ihist.Plan(H, W, NBINS, layout)
+    plain_ms = time_plain(plan)
+    plan_ov = ihist.Plan(H, W, NBINS, layout, tune={"overlap": 1})
+    overlap_ms = time_plain(plan_ov)
 
     # ---- end-to-end: pinned host frames -> copy stream -> batched compute ->
     # batched query -> host; two 32-frame batches alternate so one batch's
@@ -666,7 +675,7 @@ def main():
     write_probe_gbs = 10 * probe.numel() * 4 / (w_start.elapsed_time(w_end) / 1000.0) / 1e9
     del probe
 
-    elapsed_ms, e2e_ms, plain_ms = max_over_ranks([elapsed_ms, e2e_ms, plain_ms], world, dev)
+    elapsed_ms, e2e_ms, plain_ms, overlap_ms = max_over_ranks([elapsed_ms, e2e_ms, plain_ms, overlap_ms], world, dev)
 
     if rank == 0:
         value = job_throughput(NFRAMES, args.steps, world, elapsed_ms)
@@ -692,6 +701,11 @@ def main():
                     "value": job_throughput(NFRAMES, pf_steps, world, plain_ms), "unit": "frames/s",
                     "steps": pf_steps, "form": "%d x (ihist_compute + ihist_query) per step" % NFRAMES,
                     "tile": plan.tune},
+                "plain_per_frame_overlapped": {
+                    "value": job_throughput(NFRAMES, pf_steps, world, overlap_ms), "unit": "frames/s",
+                    "steps": pf_steps, "form": "as plain_per_frame, plan tune overlap=1 (programmatic "
+                                               "dependent launch: each scan starts while the kernel before it "
+                                               "finishes)"},
             },
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(),

@@ -54,10 +54,13 @@ struct ihist_plan_s {
   int ctas_per_sm;
   unsigned int timeout_us;
   int fault_skip_band;
+  int overlap;          // launch with programmatic dependent launch
   size_t smem_bytes;
   void *ws;
   size_t ws_bytes;
   Ctrl *ctrl;
+  Ctrl *ctrl_alt;  // control block of every other launch (epochs of the other parity)
+  unsigned long long launches;
   uint32_t *flags, *agg_cnt, *agg_left, *incl;
   cudaEvent_t ev_uploaded[2];  // sequence pipeline: slot filled
   cudaEvent_t ev_consumed[2];  // sequence pipeline: slot read by its compute
@@ -195,6 +198,7 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
     return IHIST_ERR_INVALID_ARG;
   if (t.ctas_per_sm < 0 || t.ctas_per_sm > 32) return IHIST_ERR_INVALID_ARG;
   if (t.groups_per_cta < 0 || t.groups_per_cta > 16) return IHIST_ERR_INVALID_ARG;
+  if (t.overlap != 0 && t.overlap != 1) return IHIST_ERR_INVALID_ARG;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return IHIST_ERR_CUDA;
@@ -251,6 +255,7 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   p->nitems = (unsigned int)p->nbands * (unsigned int)p->ngsets;
   p->timeout_us = t.timeout_us;
   p->fault_skip_band = t.fault_skip_band >= 1 ? t.fault_skip_band - 1 : -1;  // 1-based in the tune struct
+  p->overlap = t.overlap;
   p->smem_bytes = smem_layout(p->NW, p->R, p->G, p->nchunks * p->gpc, pm_staged(layout, p->G)).bytes;
   const int occ = p->smem_bytes <= optin ? occupancy(fn, p->NW * 32, p->smem_bytes) : 0;
   if (occ < 1) {
@@ -263,6 +268,8 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   const size_t nci = (size_t)p->nbands * p->ngroups * p->nchunks;
   size_t off = 0;
   const size_t o_ctrl = off;
+  off = align_up(off + sizeof(Ctrl), 256);
+  const size_t o_ctrl_alt = off;
   off = align_up(off + sizeof(Ctrl), 256);
   const size_t o_flags = off;
   off = align_up(off + nci * sizeof(uint32_t), 256);
@@ -285,6 +292,7 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   }
   char *base = static_cast<char *>(p->ws);
   p->ctrl = reinterpret_cast<Ctrl *>(base + o_ctrl);
+  p->ctrl_alt = reinterpret_cast<Ctrl *>(base + o_ctrl_alt);
   p->flags = reinterpret_cast<uint32_t *>(base + o_flags);
   p->agg_cnt = reinterpret_cast<uint32_t *>(base + o_cnt);
   p->agg_left = reinterpret_cast<uint32_t *>(base + o_left);
@@ -294,7 +302,12 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   uint32_t host_lut[256];
   for (int v = 0; v < 256; ++v)
     host_lut[v] = table && bin_map[v] >= 0 ? 8u * (uint32_t)bin_map[v] : kNoBin;
+  // Launches alternate between the two control blocks and each advances its
+  // block's epoch by 2, so the epochs of neighbouring launches (which may
+  // run at the same time with overlap on) never match each other's flags.
+  const unsigned int epoch_alt = 1u;
   if (cudaMemset(p->ws, 0, o_cnt) != cudaSuccess ||
+      cudaMemcpy(&p->ctrl_alt->epoch, &epoch_alt, sizeof(epoch_alt), cudaMemcpyHostToDevice) != cudaSuccess ||
       (table && cudaMemcpy(p->lut, host_lut, sizeof(host_lut), cudaMemcpyHostToDevice) != cudaSuccess) ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
@@ -390,6 +403,7 @@ extern "C" int ihist_plan_get_tune(ihist_plan_t p, ihist_tune_t *out) {
   out->fault_skip_band = p->fault_skip_band + 1;  // 0 = off
   out->groups_per_cta = p->gpc;
   out->warps_per_cta = p->NW;
+  out->overlap = p->overlap;
   return IHIST_OK;
 }
 
@@ -426,8 +440,12 @@ static const CUtensorMap *input_map(ihist_plan_s *p, const uint8_t *d_in, size_t
   return e.ok ? &e.map : nullptr;
 }
 
-extern "C" int ihist_compute(ihist_plan_t p, const uint8_t *d_in, size_t in_pitch, uint32_t *d_out,
-                             void *stream) {
+// One frame (ihist_compute).  overlap: launch with programmatic stream
+// serialization, so the grid may start while the previous kernel on the
+// stream finishes; the kernel waits for it (griddepcontrol.wait) before its
+// first store, after staging and counting its first band.
+static int compute_frame(ihist_plan_s *p, const uint8_t *d_in, size_t in_pitch, uint32_t *d_out,
+                         void *stream, bool overlap) {
   if (!p || !d_in || !d_out) return IHIST_ERR_INVALID_ARG;
   const size_t row_bytes = (size_t)p->W * (size_t)ihist_plan_channels(p);
   if (in_pitch < row_bytes || in_pitch > (size_t)LLONG_MAX) return IHIST_ERR_INVALID_ARG;
@@ -444,6 +462,7 @@ extern "C" int ihist_compute(ihist_plan_t p, const uint8_t *d_in, size_t in_pitc
     if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
     d_in = p->idx;
     in_pitch = p->idx_pitch;
+    overlap = false;  // the scan reads the plane the kernel just launched writes
   }
   const bool vec = (p->W % 4 == 0) && ((uintptr_t)d_out % 16 == 0);
   const CUtensorMap *tm = input_map(p, d_in, in_pitch);
@@ -481,9 +500,28 @@ extern "C" int ihist_compute(ihist_plan_t p, const uint8_t *d_in, size_t in_pitc
       std::min<unsigned int>(p->nitems, (unsigned int)(p->ctas_per_sm * p->sms));
   ScanFn fn = scan_fn(p->G, mmax_for(p->m), tm != nullptr, vec, p->binning == kTable);
   const unsigned long long timeout_ns = (unsigned long long)p->timeout_us * 1000ull;
-  fn<<<grid, p->NW * 32, p->smem_bytes, (cudaStream_t)stream>>>(f, tmap, p->ctrl, timeout_ns);
-  if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
+  Ctrl *ctrl = (p->launches++ & 1ull) ? p->ctrl_alt : p->ctrl;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(p->NW * 32);
+  cfg.dynamicSmemBytes = p->smem_bytes;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = overlap ? 1 : 0;
+  if (cudaLaunchKernelEx(&cfg, fn, f, tmap, ctrl, timeout_ns) != cudaSuccess) {
+    cudaGetLastError();
+    return IHIST_ERR_CUDA;
+  }
   return IHIST_OK;
+}
+
+extern "C" int ihist_compute(ihist_plan_t p, const uint8_t *d_in, size_t in_pitch, uint32_t *d_out,
+                             void *stream) {
+  return compute_frame(p, d_in, in_pitch, d_out, stream, p && p->overlap != 0);
 }
 
 int ihist::host::launch_query(int H, int W, int B, int layout, int sms, Ctrl *ctrl, const uint32_t *d_hist,
@@ -586,7 +624,8 @@ extern "C" int ihist_sequence_host(ihist_plan_t p, const uint8_t *h_frames, size
     if (cudaStreamWaitEvent(s, p->ev_uploaded[slot], 0) != cudaSuccess) return IHIST_ERR_CUDA;
     uint32_t *d_out = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(d_outs) +
                                                    (size_t)(i % nouts) * obytes);
-    rc = ihist_compute(p, d_in, row_bytes, d_out, stream);
+    // frames arrive by copy, so no kernel before a compute writes its frame
+    rc = compute_frame(p, d_in, row_bytes, d_out, stream, true);
     if (rc != IHIST_OK) return rc;
     if (cudaEventRecord(p->ev_consumed[slot], s) != cudaSuccess) return IHIST_ERR_CUDA;
     if (nrects > 0) {
@@ -618,7 +657,12 @@ extern "C" int ihist_status(ihist_plan_t p, void *stream, int *device_status) {
   if (!p || !device_status) return IHIST_ERR_INVALID_ARG;
   int rc = check_device(p);
   if (rc != IHIST_OK) return rc;
-  return read_status(p->ctrl, stream, device_status);
+  int st_alt = 0;
+  rc = read_status(p->ctrl_alt, stream, &st_alt);
+  if (rc != IHIST_OK) return rc;
+  rc = read_status(p->ctrl, stream, device_status);  // also the queries' status
+  if (rc == IHIST_OK && *device_status == IHIST_OK) *device_status = st_alt;
+  return rc;
 }
 
 extern "C" void ihist_destroy(ihist_plan_t p) {

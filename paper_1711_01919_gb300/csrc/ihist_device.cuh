@@ -85,6 +85,14 @@ __device__ __forceinline__ void st_stream(uint32_t *p, uint32_t a) {
   asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(a) : "memory");
 }
 
+// Programmatic dependent launch: wait until the grids this one depends on
+// have completed (a no-op without such a dependency), then let the next
+// grid's CTAs start.
+__device__ __forceinline__ void griddep_wait_and_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

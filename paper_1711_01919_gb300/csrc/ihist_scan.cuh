@@ -232,7 +232,8 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
                                              unsigned int it, uint32_t epoch, Ctrl *ctrl,
                                              unsigned long long timeout_ns, uint8_t *s_tiles,
                                              uint32_t *s_row, uint32_t *s_ctot, uint64_t *s_bar,
-                                             const uint32_t *s_lut, uint4 *s_stage, uint32_t &phase) {
+                                             const uint32_t *s_lut, uint4 *s_stage, uint32_t &phase,
+                                             bool &dep_pending) {
   constexpr int GQ = G / 4;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -314,6 +315,12 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
     }
   }
 
+  // the previous grid on the stream must be complete before the first
+  // store to the carries or the output
+  if (dep_pending) {
+    griddep_wait_and_release();
+    dep_pending = false;
+  }
   // per-chunk band totals and the column-count aggregate of each chunk
 #pragma unroll
   for (int cc = 0; cc < MMAX; ++cc) {
@@ -633,6 +640,7 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_lut[i] = __ldg(f.lut + i);
   if (TMA) mbar_init_fence();
   uint32_t phase = 0;
+  bool dep_pending = true;  // griddepcontrol.wait not yet done by this thread
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(&ctrl->ticket, 1u);
     __syncthreads();
@@ -641,7 +649,7 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     __syncthreads();
     if (it >= f.nitems) break;
     process_item<G, MMAX, TMA, VEC, LUT>(f, &tmap, it, epoch, ctrl, timeout_ns, s_tiles, s_row, s_ctot,
-                                         s_bar, s_lut, s_stage, phase);
+                                         s_bar, s_lut, s_stage, phase, dep_pending);
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -651,7 +659,7 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
       ctrl->ticket = 0u;
       ctrl->done = 0u;
       __threadfence();
-      atomicAdd(&ctrl->epoch, 1u);
+      atomicAdd(&ctrl->epoch, 2u);
     }
   }
 }
@@ -685,6 +693,7 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
   if (TMA) mbar_init_fence();
   const unsigned int total = ld_relaxed_u32(item_end + nframes - 1);
   uint32_t phase = 0;
+  bool dep_pending = true;  // griddepcontrol.wait not yet done by this thread
   for (;;) {
     if (threadIdx.x == 0) {
       const unsigned int t = atomicAdd(&ctrl->ticket, 1u);
@@ -713,7 +722,7 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     uint4 *s_stage = (stage != 0 && pm_staged(s_f.layout, G)) ? reinterpret_cast<uint4 *>(base + L.stage_off)
                                                                : nullptr;
     process_item<G, MMAX, TMA, VEC, false>(s_f, tmaps + fi, it, epoch, ctrl, timeout_ns, s_tiles, s_row,
-                                           s_ctot, s_bar, nullptr, s_stage, phase);
+                                           s_ctot, s_bar, nullptr, s_stage, phase, dep_pending);
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -723,7 +732,7 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
       ctrl->ticket = 0u;
       ctrl->done = 0u;
       __threadfence();
-      atomicAdd(&ctrl->epoch, 1u);
+      atomicAdd(&ctrl->epoch, 2u);
     }
   }
 }

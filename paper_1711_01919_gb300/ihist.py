@@ -59,7 +59,8 @@ class ihist_tune_t(ctypes.Structure):
         ("fault_skip_band", ctypes.c_int),
         ("groups_per_cta", ctypes.c_int),
         ("warps_per_cta", ctypes.c_int),
-        ("reserved", ctypes.c_int * 2),
+        ("overlap", ctypes.c_int),
+        ("reserved", ctypes.c_int),
     ]
 
 
@@ -76,7 +77,7 @@ class ihist_frame_t(ctypes.Structure):
 
 
 TUNE_FIELDS = ("rows_per_band", "bins_per_cta", "chunks_per_warp", "ctas_per_sm", "timeout_us",
-               "fault_skip_band", "groups_per_cta", "warps_per_cta")
+               "fault_skip_band", "groups_per_cta", "warps_per_cta", "overlap")
 
 _lock = threading.Lock()
 _lib = None

@@ -52,7 +52,7 @@ def test_plan_rejects_bad_shapes_before_touching_cuda(lib, h, w, b, layout):
 
 
 def test_plan_rejects_bad_tuning(lib):
-    for tune in ({"rows_per_band": 256}, {"bins_per_cta": 5}, {"chunks_per_warp": 3}):
+    for tune in ({"rows_per_band": 256}, {"bins_per_cta": 5}, {"chunks_per_warp": 3}, {"overlap": 2}, {"overlap": -1}):
         with pytest.raises(ihist.IhistError) as e:
             ihist.ihist_plan_tuned(16, 16, 4, 0, tune)
         assert e.value.code == ihist.IHIST_ERR_INVALID_ARG
