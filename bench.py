@@ -497,6 +497,25 @@ def other_bins_report(d_frames, outs, stream, steps: int = 5) -> dict:
                      "form": "%d x ihist_compute per step" % n, "tile": plan.tune}
         plan.close()
     del rgb
+    # the same edges on the same frames in one batched launch (a table batch)
+    with ihist.Batch([d_frames[f] for f in range(n)], NBINS, outs=[outs[f] for f in range(n)],
+                     tables=[ihist.edges_table(edges)] * n) as batch:
+        for _ in range(3):
+            batch.compute(stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            batch.compute(stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if batch.status() != ihist.IHIST_OK:
+            raise SystemExit("device status error in the batched edges run")
+        sec = a.elapsed_time(b) / 1000.0
+        byts = steps * n * (H * W * NBINS * 4 + H * W)
+        out["edges_64_nonuniform_batched"] = {"frames_per_s": steps * n / sec, "gbs": byts / sec / 1e9,
+                                              "form": "one ihist_batch_compute launch over %d frames per step, "
+                                                      "value -> bin tables" % n, "tune": batch.tune}
     return out
 
 

@@ -89,21 +89,23 @@ typedef struct ihist_plan_s *ihist_plan_t;
  *                   bins per CTA).
  *                   Plans derive it from the tiling, ignore it on input
  *                   and report it in ihist_plan_get_tune.
- *   overlap         plans: 1 = programmatic dependent launch.  Each
- *                   ihist_compute grid may start while the kernel launched
- *                   just before it on the stream is still finishing: its
- *                   CTAs stage and count their first band of the frame,
- *                   then wait for that kernel to complete before their
- *                   first store (carries or output).  So the frame (d_in)
- *                   must not be written by the kernel launched just before
- *                   ihist_compute on the same stream; a copy, an event wait
- *                   or another kernel in between makes it safe again.  Saves
- *                   the gap between back-to-back launches (1080p x 64:
- *                   116 -> 98 us per frame).  0 = off (default).  Joint
- *                   plans ignore it (their scan reads the joint-bin plane
- *                   the kernel before it writes); ihist_sequence_host
- *                   always overlaps its launches (its frames arrive by copy).
- *                   Batches ignore it.                                    */
+ *   overlap         plans: every ihist_compute (and ihist_query) is launched
+ *                   with programmatic dependent launch, so its CTAs may
+ *                   start while the kernel launched just before it on the
+ *                   stream is still finishing.  By default (0) a scan's CTAs
+ *                   take their first work item and then wait for that kernel
+ *                   to complete before reading anything of the frame, which
+ *                   is always safe.  1 = overlap further: they stage and
+ *                   count their first band of the frame before waiting (every
+ *                   store still waits), so the frame (d_in) must not be
+ *                   written by the kernel launched just before ihist_compute
+ *                   on the same stream (a copy, an event wait or another
+ *                   kernel in between makes it safe again).  1080p x 64 per
+ *                   frame, back to back: 115 us plain launches, 104 us with
+ *                   the default, 99 us with 1.  Joint plans treat 1 as 0
+ *                   (their scan reads the joint-bin plane the kernel before
+ *                   it writes); ihist_sequence_host always uses 1 (its
+ *                   frames arrive by copy).  Batches ignore it.            */
 typedef struct {
   int rows_per_band;
   int bins_per_cta;
@@ -200,7 +202,9 @@ int ihist_compute(ihist_plan_t plan, const uint8_t *d_in, size_t in_pitch, uint3
  * plan's layout and shape.  d_rects: n x {x0, y0, x1, y1} int32, inclusive,
  * x = column.  d_hist_out: n x nbins uint32, row i = histogram of rect i.
  * A rectangle with x0 > x1, y0 > y1 or a corner outside the frame yields a
- * zero row and latches IHIST_ERR_BAD_RECT.  n == 0 is a no-op. */
+ * zero row and latches IHIST_ERR_BAD_RECT.  n == 0 is a no-op.  The
+ * launch may start while the kernel before it on the stream finishes; it
+ * waits for that kernel before reading anything. */
 int ihist_query(ihist_plan_t plan, const uint32_t *d_hist, const int32_t *d_rects, int n,
                 uint32_t *d_hist_out, void *stream);
 
@@ -281,12 +285,17 @@ typedef struct ihist_batch_s *ihist_batch_t;
 
 /* One frame of a batch.  d_in: h rows of w bytes, row stride in_pitch;
  * d_out: ihist_output_bytes(h, w, nbins) bytes in `layout`.  Both are device
- * pointers the caller owns and keeps valid while the batch may run. */
+ * pointers the caller owns and keeps valid while the batch may run.
+ * bin_of_value: NULL for uniform bins, or a HOST array of 256 ints as for
+ * ihist_plan_lut (bin of each intensity in [0, nbins), -1 = no bin; bins by
+ * edges are such a table), read during ihist_batch_plan / ihist_batch_set_io
+ * and copied into the batch. */
 typedef struct {
   int h, w, nbins, layout;
   const uint8_t *d_in;
   size_t in_pitch;
   uint32_t *d_out;
+  const int *bin_of_value;
 } ihist_frame_t;
 
 /* Plan a batch of n >= 1 frames (limits per frame as for ihist_plan); the
@@ -299,8 +308,15 @@ typedef struct {
  * IHIST_ERR_UNSUPPORTED (at most 8192 columns with 16 warps).  Frames bound
  * later by ihist_batch_set_io keep within the launch shape the planned
  * frames fixed (chunks per warp, carry width per CTA), which may leave some
- * of a narrower frame's CTA idle.  Allocates the batch's device workspace
- * and pinned staging buffers. */
+ * of a narrower frame's CTA idle.  If any planned frame has a bin table
+ * (bin_of_value), the batch is a table batch: every frame bins through a
+ * per-slot table in shared memory (uniform frames get the table of
+ * floor(v * nbins / 256)), bins_per_cta is 4 or 8 (default 8 when a frame is
+ * pixel-major; 16 gives IHIST_ERR_UNSUPPORTED) and later bindings may mix
+ * table and uniform frames; a batch planned without tables refuses tables
+ * later (IHIST_ERR_UNSUPPORTED).  A table entry outside [-1, nbins) gives
+ * IHIST_ERR_INVALID_ARG.  Allocates the batch's device workspace and pinned
+ * staging buffers. */
 int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_tune_t *tune,
                      ihist_batch_t *out);
 

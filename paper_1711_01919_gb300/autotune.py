@@ -68,10 +68,10 @@ def plan_candidates(h: int, w: int, nbins: int):
     return out
 
 
-def batch_candidates(shapes=()):
+def batch_candidates(shapes=(), tables=False):
     """Batch launch shapes to time (the default first); 16-bin groups too
     when some frame is pixel-major (their longer pieces of pixel records)."""
-    gs = (4, 8, 16) if any(s[3] == ihist.IHIST_PIXEL_MAJOR for s in shapes) else (4, 8)
+    gs = (4, 8, 16) if any(s[3] == ihist.IHIST_PIXEL_MAJOR for s in shapes) and not tables else (4, 8)
     return [{}] + [{"warps_per_cta": nw, "bins_per_cta": G, "rows_per_band": R}
                    for nw in (8, 16) for G in gs for R in (24, 32, 40, 48, 56)]
 
@@ -102,11 +102,13 @@ def time_plan(h, w, nbins, layout, tune, reps=5):
     return statistics.median(ms)
 
 
-def time_batch(shapes, tune, reps=3):
-    """Median ms of one batched launch over frames of these (h, w, nbins, layout)."""
+def time_batch(shapes, tune, reps=3, tables=False):
+    """Median ms of one batched launch over frames of these (h, w, nbins,
+    layout); tables: every frame bins through a value -> bin table."""
     import torch
     frames = [torch.from_numpy(synth.uniform_frame(100 + i, h, w)).cuda() for i, (h, w, b, l) in enumerate(shapes)]
-    with ihist.Batch(frames, [s[2] for s in shapes], [s[3] for s in shapes], tune=tune or None) as batch:
+    tb = [[(v * s[2]) >> 8 for v in range(256)] for s in shapes] if tables else None
+    with ihist.Batch(frames, [s[2] for s in shapes], [s[3] for s in shapes], tune=tune or None, tables=tb) as batch:
         for _ in range(2):
             batch.compute()
         ms = []
@@ -156,18 +158,19 @@ def tune_plan(h, w, nbins, layout=ihist.IHIST_BIN_MAJOR, timer=None, device=None
     return best
 
 
-def tune_batch(shapes, timer=None, device=None, use_cache=True):
-    """Best (warps_per_cta, bins_per_cta, rows_per_band) for a batch of (h, w, nbins, layout) frames."""
+def tune_batch(shapes, timer=None, device=None, use_cache=True, tables=False):
+    """Best (warps_per_cta, bins_per_cta, rows_per_band) for a batch of (h, w,
+    nbins, layout) frames; tables: a table batch (other bin structures)."""
     device = device or _device_key()
     sig = ",".join("%dx%dx%dx%d" % tuple(s) for s in sorted(set(tuple(s) for s in shapes)))
-    key = "batch|%s|%d|%s" % (device, len(shapes), sig)
+    key = "batch|%s|%d|%s%s" % (device, len(shapes), sig, "|tables" if tables else "")
     path = cache_path()
     with _lock:
         cache = _load_cache(path) if use_cache else {}
         if key in cache:
             return cache[key]["tune"]
-    timer = timer or (lambda t: time_batch(shapes, t))
-    best, ms, _ = _search(batch_candidates(shapes), timer)
+    timer = timer or (lambda t: time_batch(shapes, t, tables=tables))
+    best, ms, _ = _search(batch_candidates(shapes, tables), timer)
     if use_cache:
         with _lock:
             cache = _load_cache(path)

@@ -440,10 +440,12 @@ static const CUtensorMap *input_map(ihist_plan_s *p, const uint8_t *d_in, size_t
   return e.ok ? &e.map : nullptr;
 }
 
-// One frame (ihist_compute).  overlap: launch with programmatic stream
-// serialization, so the grid may start while the previous kernel on the
-// stream finishes; the kernel waits for it (griddepcontrol.wait) before its
-// first store, after staging and counting its first band.
+// One frame (ihist_compute).  Every scan is launched with programmatic
+// stream serialization, so its CTAs may start while the previous kernel on
+// the stream finishes; they take their first work item and then wait for
+// that kernel (griddepcontrol.wait) before reading the frame, or, with
+// overlap, only before their first store, after staging and counting their
+// first band.
 static int compute_frame(ihist_plan_s *p, const uint8_t *d_in, size_t in_pitch, uint32_t *d_out,
                          void *stream, bool overlap) {
   if (!p || !d_in || !d_out) return IHIST_ERR_INVALID_ARG;
@@ -492,6 +494,7 @@ static int compute_frame(ihist_plan_s *p, const uint8_t *d_in, size_t in_pitch, 
   f.ngsets = p->ngsets;
   f.fault_skip_band = p->fault_skip_band;
   f.nitems = p->nitems;
+  f.late_wait = overlap ? 1 : 0;
   f.agg_cnt = p->agg_cnt;
   f.agg_left = p->agg_left;
   f.incl = p->incl;
@@ -511,7 +514,7 @@ static int compute_frame(ihist_plan_s *p, const uint8_t *d_in, size_t in_pitch, 
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = overlap ? 1 : 0;
+  cfg.numAttrs = 1;
   if (cudaLaunchKernelEx(&cfg, fn, f, tmap, ctrl, timeout_ns) != cudaSuccess) {
     cudaGetLastError();
     return IHIST_ERR_CUDA;
@@ -536,13 +539,25 @@ int ihist::host::launch_query(int H, int W, int B, int layout, int sms, Ctrl *ct
   const unsigned int threads = 256;
   const unsigned int grid =
       std::min<unsigned int>((total + threads - 1) / threads, (unsigned int)sms * 16u);
-  if (layout == IHIST_BIN_MAJOR)
-    query_kernel<0><<<grid, threads, 0, (cudaStream_t)stream>>>(d_hist, H, W, B, d_rects, total,
-                                                                d_hist_out, ctrl);
-  else
-    query_kernel<1><<<grid, threads, 0, (cudaStream_t)stream>>>(d_hist, H, W, B, d_rects, total,
-                                                                d_hist_out, ctrl);
-  if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
+  // may start while the kernel before it finishes; waits for it first thing
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e =
+      layout == IHIST_BIN_MAJOR
+          ? cudaLaunchKernelEx(&cfg, query_kernel<0>, d_hist, H, W, B, d_rects, total, d_hist_out, ctrl)
+          : cudaLaunchKernelEx(&cfg, query_kernel<1>, d_hist, H, W, B, d_rects, total, d_hist_out, ctrl);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return IHIST_ERR_CUDA;
+  }
   return IHIST_OK;
 }
 

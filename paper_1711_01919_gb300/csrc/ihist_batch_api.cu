@@ -89,6 +89,26 @@ bool frame_vec_ok(const ihist_frame_t &fr) {
   return fr.w % 4 == 0 && !((uintptr_t)fr.d_out & 15u);
 }
 
+// A frame's value -> bin table, if it has one, maps every value to a bin
+// in [0, nbins) or to -1 (no bin).
+bool table_ok(const ihist_frame_t &fr) {
+  if (!fr.bin_of_value) return true;
+  for (int v = 0; v < 256; ++v)
+    if (fr.bin_of_value[v] < -1 || fr.bin_of_value[v] >= fr.nbins) return false;
+  return true;
+}
+
+// The kernel's form of a frame's binning: 8 * bin of each value, or kNoBin;
+// uniform frames of a table batch get the table of q = floor(v * B / 256).
+void fill_table(const ihist_frame_t &fr, uint32_t *dst) {
+  for (int v = 0; v < 256; ++v) {
+    if (fr.bin_of_value)
+      dst[v] = fr.bin_of_value[v] >= 0 ? 8u * (uint32_t)fr.bin_of_value[v] : kNoBin;
+    else
+      dst[v] = 8u * (((uint32_t)v * (uint32_t)fr.nbins) >> 8);
+  }
+}
+
 }  // namespace
 
 struct ihist_batch_s {
@@ -96,6 +116,7 @@ struct ihist_batch_s {
   int fault_skip_band;  // test hook, -1 off
   int ctas_per_sm[2][2];  // occupancy of each (tma, vec) variant
   bool tma, vec;          // variant the current frames allow
+  bool lut;               // frames bin through per-slot value -> bin tables
   unsigned int timeout_us, total;
   size_t smem_bytes, ws_bytes;
   unsigned long long bins_total;
@@ -104,6 +125,7 @@ struct ihist_batch_s {
   FrameDesc *d_fd;
   CUtensorMap *d_tm;
   unsigned int *d_end, *d_bins_end;
+  uint32_t *d_lut;                                    // table batches: [slot][256]
   std::vector<size_t> slot_nci;                       // carry capacity of each slot
   std::vector<uint32_t *> slot_flags, slot_cnt, slot_left, slot_incl;
   std::vector<FrameDesc> fd;                          // current frames
@@ -111,6 +133,7 @@ struct ihist_batch_s {
   FrameDesc *h_fd;           // pinned staging
   CUtensorMap *h_tm;
   unsigned int *h_end, *h_bins_end;
+  uint32_t *h_lut;
   cudaEvent_t staged;        // last staging copy done
   cudaEvent_t uploaded, computed;
   bool launched;
@@ -141,8 +164,9 @@ static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames, int n) {
     int rc = validate_shape(fr.h, fr.w, fr.nbins, fr.layout);
     if (rc != IHIST_OK) return rc;
     if (!fr.d_in || !fr.d_out || fr.in_pitch < (size_t)fr.w || ((uintptr_t)fr.d_out & 3u) ||
-        fr.in_pitch > (size_t)LLONG_MAX)
+        fr.in_pitch > (size_t)LLONG_MAX || !table_ok(fr))
       return IHIST_ERR_INVALID_ARG;
+    if (fr.bin_of_value && !b->lut) return IHIST_ERR_UNSUPPORTED;  // planned without tables
     FrameDesc &f = fd[i];
     if (!batch_frame_tiling(fr.h, fr.w, fr.nbins, fr.layout, b->G, b->R_req, b->mmax, b->ncg_max, b->warps,
                             &f) ||
@@ -176,6 +200,10 @@ static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames, int n) {
     brun += (unsigned long long)frames[i].nbins;
     b->h_end[i] = (unsigned int)run;
     b->h_bins_end[i] = (unsigned int)brun;
+    if (b->lut) {
+      fill_table(frames[i], b->h_lut + (size_t)i * 256);
+      fd[i].lut = b->d_lut + (size_t)i * 256;
+    }
     b->h_fd[i] = fd[i];
   }
   b->fd.assign(fd.begin(), fd.end());
@@ -195,6 +223,8 @@ static int batch_upload(ihist_batch_s *b, cudaStream_t s) {
       cudaMemcpyAsync(b->d_end, b->h_end, (size_t)n * sizeof(unsigned int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(b->d_bins_end, b->h_bins_end, (size_t)n * sizeof(unsigned int), cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
+      (b->lut && cudaMemcpyAsync(b->d_lut, b->h_lut, (size_t)n * 256 * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                 s) != cudaSuccess) ||
       cudaEventRecord(b->staged, s) != cudaSuccess)
     return IHIST_ERR_CUDA;
   return IHIST_OK;
@@ -213,6 +243,7 @@ extern "C" void ihist_batch_destroy(ihist_batch_t b) {
   if (b->h_tm) cudaFreeHost(b->h_tm);
   if (b->h_end) cudaFreeHost(b->h_end);
   if (b->h_bins_end) cudaFreeHost(b->h_bins_end);
+  if (b->h_lut) cudaFreeHost(b->h_lut);
   if (b->ws) cudaFree(b->ws);
   if (prev != b->device && prev >= 0) cudaSetDevice(prev);
   delete b;
@@ -224,11 +255,15 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   ihist_tune_t t;
   std::memset(&t, 0, sizeof(t));
   if (tune) t = *tune;
+  // frames with value -> bin tables make a table batch (every frame bins
+  // through a table; 4 or 8 bins per CTA)
+  bool lut = false;
+  for (int i = 0; i < n; ++i) lut = lut || frames[i].bin_of_value != nullptr;
   if (t.bins_per_cta == 0) {
     // larger bin groups when any frame is pixel-major (longer contiguous
     // pieces per pixel record): 16 when every frame has at least 16 bins and
     // fits 16 warps x 2 chunks, else 8
-    bool pm = false, wide16 = true;
+    bool pm = false, wide16 = !lut;
     for (int i = 0; i < n; ++i) {
       pm = pm || frames[i].layout == IHIST_PIXEL_MAJOR;
       wide16 = wide16 && frames[i].nbins >= 16 && frames[i].w <= kBatchWarps * 2 * kChunk;
@@ -236,6 +271,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
     t.bins_per_cta = pm ? (wide16 ? 16 : 8) : 4;
   }
   if (t.bins_per_cta != 4 && t.bins_per_cta != 8 && t.bins_per_cta != 16) return IHIST_ERR_INVALID_ARG;
+  if (lut && t.bins_per_cta == 16) return IHIST_ERR_UNSUPPORTED;
   if (t.rows_per_band < 0 || t.rows_per_band > 255) return IHIST_ERR_INVALID_ARG;
   if (t.ctas_per_sm < 0 || t.ctas_per_sm > 32) return IHIST_ERR_INVALID_ARG;
   if (t.warps_per_cta != 0 && t.warps_per_cta != 4 && t.warps_per_cta != 8 && t.warps_per_cta != 16)
@@ -243,6 +279,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   for (int i = 0; i < n; ++i) {
     const int rc = validate_shape(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout);
     if (rc != IHIST_OK) return rc;
+    if (!table_ok(frames[i])) return IHIST_ERR_INVALID_ARG;
   }
   int dev = 0, sms = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return IHIST_ERR_CUDA;
@@ -256,6 +293,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   b->sms = sms;
   b->cap = n;
   b->G = t.bins_per_cta;
+  b->lut = lut;
   b->fault_skip_band = t.fault_skip_band >= 1 ? t.fault_skip_band - 1 : -1;
   // pixel-major frames stage their rows in shared memory
   b->stage = 0;
@@ -279,7 +317,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   for (int mm = 1; mm <= max_m; mm <<= 1)
     for (int tma = 0; tma < 2; ++tma)
       for (int vec = 0; vec < 2; ++vec) {
-        BatchFn fn = batch_fn(b->G, mm, tma != 0, vec != 0);
+        BatchFn fn = batch_fn(b->G, mm, tma != 0, vec != 0, b->lut);
         cudaFuncAttributes a;
         if (!fn || cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
           cudaGetLastError();
@@ -322,7 +360,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
       }
       int occ = 0;
       const size_t smem = smem_layout(b->warps, rmax, b->G, ncg, b->stage != 0).bytes;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_fn(b->G, mmax_for(mm), true, true),
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_fn(b->G, mmax_for(mm), true, true, b->lut),
                                                         b->warps * 32, smem) != cudaSuccess) {
         cudaGetLastError();
         occ = 0;
@@ -355,7 +393,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   b->smem_bytes = smem_layout(b->warps, b->R_max, b->G, b->ncg_max, b->stage != 0).bytes;
   for (int tma = 0; tma < 2; ++tma)
     for (int vec = 0; vec < 2; ++vec) {
-      BatchFn fn = batch_fn(b->G, b->mmax, tma != 0, vec != 0);
+      BatchFn fn = batch_fn(b->G, b->mmax, tma != 0, vec != 0, b->lut);
       cudaFuncAttributes a;
       if (!fn || cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
         cudaGetLastError();
@@ -391,6 +429,8 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   off = align_up(off + (size_t)n * sizeof(unsigned int), 256);
   const size_t o_bend = off;
   off = align_up(off + (size_t)n * sizeof(unsigned int), 256);
+  const size_t o_lut = off;
+  if (lut) off = align_up(off + (size_t)n * 256 * sizeof(uint32_t), 256);
   const size_t o_carry = off;
   for (int i = 0; i < n; ++i) {
     const size_t nci = b->slot_nci[i];
@@ -404,6 +444,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
       cudaMallocHost((void **)&b->h_tm, (size_t)n * sizeof(CUtensorMap)) != cudaSuccess ||
       cudaMallocHost((void **)&b->h_end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
       cudaMallocHost((void **)&b->h_bins_end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
+      (lut && cudaMallocHost((void **)&b->h_lut, (size_t)n * 256 * sizeof(uint32_t)) != cudaSuccess) ||
       cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->computed, cudaEventDisableTiming) != cudaSuccess) {
@@ -417,6 +458,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   b->d_tm = reinterpret_cast<CUtensorMap *>(base + o_tm);
   b->d_end = reinterpret_cast<unsigned int *>(base + o_end);
   b->d_bins_end = reinterpret_cast<unsigned int *>(base + o_bend);
+  if (lut) b->d_lut = reinterpret_cast<uint32_t *>(base + o_lut);
   size_t fo = o_flags, co = o_carry;
   for (int i = 0; i < n; ++i) {
     const size_t nci = b->slot_nci[i];
@@ -482,7 +524,7 @@ extern "C" int ihist_batch_compute(ihist_batch_t b, void *stream) {
   if (!b) return IHIST_ERR_INVALID_ARG;
   int rc = check_batch_device(b);
   if (rc != IHIST_OK) return rc;
-  BatchFn fn = batch_fn(b->G, b->mmax, b->tma, b->vec);
+  BatchFn fn = batch_fn(b->G, b->mmax, b->tma, b->vec, b->lut);
   const int cps = b->ctas_per_sm[b->tma ? 1 : 0][b->vec ? 1 : 0];
   const unsigned int grid = std::min<unsigned int>(b->total, (unsigned int)(cps * b->sms));
   const unsigned long long timeout_ns = (unsigned long long)b->timeout_us * 1000ull;

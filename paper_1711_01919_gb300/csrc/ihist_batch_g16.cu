@@ -7,8 +7,8 @@ namespace ihist {
 namespace {
 template <int MMAX>
 BatchFn pick(bool tma, bool vec) {
-  if (tma) return vec ? batch_kernel<16, MMAX, true, true> : batch_kernel<16, MMAX, true, false>;
-  return vec ? batch_kernel<16, MMAX, false, true> : batch_kernel<16, MMAX, false, false>;
+  if (tma) return vec ? batch_kernel<16, MMAX, true, true, false> : batch_kernel<16, MMAX, true, false, false>;
+  return vec ? batch_kernel<16, MMAX, false, true, false> : batch_kernel<16, MMAX, false, false, false>;
 }
 }  // namespace
 

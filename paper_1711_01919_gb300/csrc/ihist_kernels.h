@@ -23,6 +23,8 @@ ScanFn scan_fn_lut_g8(int mmax, bool tma, bool vec);
 BatchFn batch_fn_g4(int mmax, bool tma, bool vec);
 BatchFn batch_fn_g8(int mmax, bool tma, bool vec);
 BatchFn batch_fn_g16(int mmax, bool tma, bool vec);  // mmax <= 2
+BatchFn batch_fn_lut_g4(int mmax, bool tma, bool vec);  // per-frame value -> bin tables
+BatchFn batch_fn_lut_g8(int mmax, bool tma, bool vec);
 
 inline ScanFn scan_fn(int G, int mmax, bool tma, bool vec, bool lut = false) {
   if (lut) return G == 4 ? scan_fn_lut_g4(mmax, tma, vec) : G == 8 ? scan_fn_lut_g8(mmax, tma, vec) : nullptr;
@@ -34,7 +36,8 @@ inline ScanFn scan_fn(int G, int mmax, bool tma, bool vec, bool lut = false) {
   }
 }
 
-inline BatchFn batch_fn(int G, int mmax, bool tma, bool vec) {
+inline BatchFn batch_fn(int G, int mmax, bool tma, bool vec, bool lut = false) {
+  if (lut) return G == 4 ? batch_fn_lut_g4(mmax, tma, vec) : G == 8 ? batch_fn_lut_g8(mmax, tma, vec) : nullptr;
   switch (G) {
     case 4: return batch_fn_g4(mmax, tma, vec);
     case 8: return batch_fn_g8(mmax, tma, vec);

@@ -19,6 +19,9 @@ __global__ void __launch_bounds__(256) query_kernel(const uint32_t *__restrict__
                                                      const int32_t *__restrict__ rects,
                                                      unsigned int total,
                                                      uint32_t *__restrict__ out, Ctrl *ctrl) {
+  // launched with programmatic stream serialization: the histogram is read
+  // only once the grid before (normally the scan that wrote it) completed
+  griddep_wait_and_release();
   const size_t plane = (size_t)H * (size_t)W;
   for (unsigned int p = blockIdx.x * blockDim.x + threadIdx.x; p < total;
        p += gridDim.x * blockDim.x) {

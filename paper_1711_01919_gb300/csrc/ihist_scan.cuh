@@ -49,7 +49,8 @@ struct FrameDesc {
   int H, W, B, layout;  // layout: 0 bin-major, 1 pixel-major
   int qmul;             // uniform bins: q = (v * qmul) >> 8; qmul = B, or 256 when
                         // the input already holds bin indices
-  int reserved_;
+  int late_wait;        // scan_kernel: 1 = wait for the previous grid only before the
+                        // first store; 0 = right after taking the first work item
   int R, nbands, ngroups, nchunks, m;
   int wpg;              // warps per bin group: ceil(nchunks / m)
   int gpc;              // bin groups per CTA (warp w serves group w / wpg)
@@ -648,6 +649,14 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     const uint32_t epoch = s_epoch;
     __syncthreads();
     if (it >= f.nitems) break;
+    // Programmatic dependent launch: by default nothing of the frame is read
+    // before the grid the launch depends on has completed; with late_wait
+    // the first band is staged and counted first (the caller guarantees
+    // that grid does not write the frame).
+    if (dep_pending && f.late_wait == 0) {
+      griddep_wait_and_release();
+      dep_pending = false;
+    }
     process_item<G, MMAX, TMA, VEC, LUT>(f, &tmap, it, epoch, ctrl, timeout_ns, s_tiles, s_row, s_ctot,
                                          s_bar, s_lut, s_stage, phase, dep_pending);
     __syncthreads();
@@ -669,8 +678,10 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
 // run frame by frame and band-major within a frame, so a CTA only waits on
 // bands of its own frame that a running CTA holds.  Per-frame descriptors
 // and TMA tensor maps live in device memory; shared memory is sized for the
-// largest frame (R_max rows, nchunk_gpc_max chunk x group columns).
-template <int G, int MMAX, bool TMA, bool VEC>
+// largest frame (R_max rows, nchunk_gpc_max chunk x group columns).  LUT:
+// every frame bins through its own value -> bin table (FrameDesc::lut),
+// copied into shared memory whenever the CTA moves to another frame.
+template <int G, int MMAX, bool TMA, bool VEC, bool LUT>
 __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     batch_kernel(const FrameDesc *frames, const CUtensorMap *__restrict__ tmaps,
                  const unsigned int *item_end, int nframes, int R_max,
@@ -679,6 +690,7 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
   __shared__ unsigned int s_item, s_epoch;
   __shared__ int s_frame;
   __shared__ __align__(16) FrameDesc s_f;
+  __shared__ uint32_t s_lut[LUT ? 256 : 1];
   const int NW = blockDim.x >> 5;
   const SmemLayout L = smem_layout(NW, R_max, G, nchunk_gpc_max, stage != 0);
   uint8_t *base = reinterpret_cast<uint8_t *>(
@@ -694,6 +706,7 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
   const unsigned int total = ld_relaxed_u32(item_end + nframes - 1);
   uint32_t phase = 0;
   bool dep_pending = true;  // griddepcontrol.wait not yet done by this thread
+  int lut_frame = -1;       // frame whose table s_lut holds
   for (;;) {
     if (threadIdx.x == 0) {
       const unsigned int t = atomicAdd(&ctrl->ticket, 1u);
@@ -715,14 +728,20 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
       const uint32_t *src = reinterpret_cast<const uint32_t *>(frames + fi);
       for (int i = threadIdx.x; i < kWords; i += blockDim.x)
         reinterpret_cast<uint32_t *>(&s_f)[i] = ld_relaxed_u32(src + i);
+      if (LUT && fi != lut_frame) {
+        const uint32_t *lut = reinterpret_cast<const uint32_t *>(ld_relaxed_u64(&frames[fi].lut));
+        const bool ok = IHIST_GUARD(ctrl, lut != nullptr);
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) s_lut[i] = ok ? ld_relaxed_u32(lut + i) : kNoBin;
+      }
     }
     __syncthreads();
     if (t >= total) break;
+    lut_frame = fi;
     const unsigned int it = t - (fi > 0 ? ld_relaxed_u32(item_end + fi - 1) : 0u);
     uint4 *s_stage = (stage != 0 && pm_staged(s_f.layout, G)) ? reinterpret_cast<uint4 *>(base + L.stage_off)
                                                                : nullptr;
-    process_item<G, MMAX, TMA, VEC, false>(s_f, tmaps + fi, it, epoch, ctrl, timeout_ns, s_tiles, s_row,
-                                           s_ctot, s_bar, nullptr, s_stage, phase, dep_pending);
+    process_item<G, MMAX, TMA, VEC, LUT>(s_f, tmaps + fi, it, epoch, ctrl, timeout_ns, s_tiles, s_row,
+                                         s_ctot, s_bar, LUT ? s_lut : nullptr, s_stage, phase, dep_pending);
     __syncthreads();
   }
   if (threadIdx.x == 0) {

@@ -73,6 +73,7 @@ class ihist_frame_t(ctypes.Structure):
         ("d_in", ctypes.c_void_p),
         ("in_pitch", ctypes.c_size_t),
         ("d_out", ctypes.c_void_p),
+        ("bin_of_value", ctypes.POINTER(ctypes.c_int)),
     ]
 
 
@@ -312,16 +313,41 @@ def ihist_destroy(plan: int) -> None:
         load().ihist_destroy(plan)
 
 
+def _table_ptr(table):
+    """A 256-entry value -> bin table as a C int array (None stays NULL)."""
+    if table is None:
+        return None
+    vals = [int(v) for v in table]
+    if len(vals) != 256:
+        raise ValueError("a bin table has 256 entries, one per intensity")
+    return ctypes.cast((ctypes.c_int * 256)(*vals), ctypes.POINTER(ctypes.c_int))
+
+
 def _frames_array(frames):
+    """frames: (h, w, nbins, layout, d_in, in_pitch, d_out[, table]) tuples."""
     arr = (ihist_frame_t * len(frames))()
     for i, fr in enumerate(frames):
-        h, w, nbins, layout, d_in, pitch, d_out = fr
-        arr[i] = ihist_frame_t(h, w, nbins, layout, d_in, pitch, d_out)
+        h, w, nbins, layout, d_in, pitch, d_out = fr[:7]
+        table = fr[7] if len(fr) > 7 else None
+        arr[i] = ihist_frame_t(h, w, nbins, layout, d_in, pitch, d_out, _table_ptr(table))
     return arr
 
 
+def edges_table(edges):
+    """Value -> bin table of bins by edges: bin k holds edges[k] <= v <
+    edges[k + 1]; values outside [edges[0], edges[-1]) are in no bin (-1)."""
+    e = [int(x) for x in edges]
+    if len(e) < 2 or any(b <= a for a, b in zip(e, e[1:])) or e[0] < 0 or e[-1] > 256:
+        raise ValueError("edges must increase strictly within [0, 256]")
+    table = [-1] * 256
+    for k in range(len(e) - 1):
+        for v in range(e[k], e[k + 1]):
+            table[v] = k
+    return table
+
+
 def ihist_batch_plan(frames, tune=None) -> int:
-    """frames: sequence of (h, w, nbins, layout, d_in, in_pitch, d_out)."""
+    """frames: sequence of (h, w, nbins, layout, d_in, in_pitch, d_out[, table])."""
     arr = _frames_array(frames)
     out = ctypes.c_void_p()
     t = _tune_struct(tune) if tune else None
@@ -530,41 +556,47 @@ class Batch:
     """Many frames (CUDA uint8 [h][w] tensors, any mix of shapes) in one
     persistent launch; outputs are int32 tensors holding uint32 counts."""
 
-    def __init__(self, frames, nbins, layouts=None, outs=None, tune=None):
+    def __init__(self, frames, nbins, layouts=None, outs=None, tune=None, tables=None):
+        """tables: None, or one entry per frame, None (uniform bins) or a
+        256-entry value -> bin table (see edges_table)."""
         import torch
         n = len(frames)
         nb = list(nbins) if hasattr(nbins, "__len__") else [nbins] * n
         ly = list(layouts) if layouts is not None else [IHIST_BIN_MAJOR] * n
         self.frames = list(frames)
         self.nbins, self.layouts = nb, ly
+        self.tables = list(tables) if tables is not None else [None] * n
         self.outs = list(outs) if outs is not None else [
             torch.empty(out_shape(f.shape[0], f.shape[1], b, l), dtype=torch.int32, device=f.device)
             for f, b, l in zip(self.frames, nb, ly)]
         if tune == "auto":
             from . import autotune
-            tune = autotune.tune_batch([(f.shape[0], f.shape[1], b, l) for f, b, l in zip(self.frames, nb, ly)])
+            tune = autotune.tune_batch([(f.shape[0], f.shape[1], b, l) for f, b, l in zip(self.frames, nb, ly)],
+                                       tables=any(t is not None for t in self.tables))
         self.handle = ihist_batch_plan(self._desc(), tune or None)
         self.tune = ihist_batch_get_tune(self.handle)
 
     def _desc(self):
         d = []
-        for f, b, l, o in zip(self.frames, self.nbins, self.layouts, self.outs):
+        for f, b, l, o, t in zip(self.frames, self.nbins, self.layouts, self.outs, self.tables):
             if f.dtype.itemsize != 1 or f.dim() != 2 or f.stride(1) != 1:
                 raise ValueError("frames must be 2-D uint8 tensors with unit column stride")
-            d.append((f.shape[0], f.shape[1], b, l, f.data_ptr(), f.stride(0), o.data_ptr()))
+            d.append((f.shape[0], f.shape[1], b, l, f.data_ptr(), f.stride(0), o.data_ptr(), t))
         return d
 
-    def set_io(self, frames, outs, nbins=None, layouts=None, stream=None):
-        """Bind new frames/outputs (any shapes that fit the planned slots)."""
+    def set_io(self, frames, outs, nbins=None, layouts=None, stream=None, tables=None):
+        """Bind new frames/outputs (any shapes that fit the planned slots);
+        tables as for the constructor (default: uniform bins)."""
         frames, outs = list(frames), list(outs)
         nb = list(nbins) if nbins is not None else self.nbins[:len(frames)]
         ly = list(layouts) if layouts is not None else self.layouts[:len(frames)]
-        old = (self.frames, self.outs, self.nbins, self.layouts)
-        self.frames, self.outs, self.nbins, self.layouts = frames, outs, nb, ly
+        tb = list(tables) if tables is not None else [None] * len(frames)
+        old = (self.frames, self.outs, self.nbins, self.layouts, self.tables)
+        self.frames, self.outs, self.nbins, self.layouts, self.tables = frames, outs, nb, ly, tb
         try:
             ihist_batch_set_io(self.handle, self._desc(), _stream(stream))
         except Exception:
-            self.frames, self.outs, self.nbins, self.layouts = old
+            self.frames, self.outs, self.nbins, self.layouts, self.tables = old
             raise
 
     def compute(self, stream=None):

@@ -113,3 +113,29 @@ def test_mapping_arguments_checked_before_touching_cuda(lib):
         # (the last: CW-STS without its workspace)
         assert lib.ihist_mapping_compute(mapping, h, w, b, ctypes.c_void_p(16), w, ctypes.c_void_p(16), None,
                                          None) == ihist.IHIST_ERR_INVALID_ARG
+
+
+def test_batch_tables_are_checked_before_touching_cuda(lib):
+    # (h, w, nbins, layout, d_in, in_pitch, d_out, table): pointers are never
+    # dereferenced because the arguments are refused first
+    good = [(v * 8) >> 8 for v in range(256)]
+    for table, code in ((good[:255] + [8], ihist.IHIST_ERR_INVALID_ARG),
+                        ([-2] + good[1:], ihist.IHIST_ERR_INVALID_ARG)):
+        with pytest.raises(ihist.IhistError) as e:
+            ihist.ihist_batch_plan([(16, 16, 8, 0, 16, 16, 16, table)])
+        assert e.value.code == code
+    with pytest.raises(ihist.IhistError) as e:  # tables need 4 or 8 bins per CTA
+        ihist.ihist_batch_plan([(16, 16, 8, 0, 16, 16, 16, good)], tune={"bins_per_cta": 16})
+    assert e.value.code == ihist.IHIST_ERR_UNSUPPORTED
+    with pytest.raises(ValueError):
+        ihist.ihist_batch_plan([(16, 16, 8, 0, 16, 16, 16, good[:100])])
+
+
+def test_edges_table_matches_the_oracle_binning():
+    import oracle
+    for edges in ([0, 256], [0, 16, 64, 128, 256], [10, 11, 200], [0, 1, 2, 255, 256]):
+        table = ihist.edges_table(edges)
+        assert table == [int(oracle.bin_of_edges(v, edges)) for v in range(256)]
+    for bad in ([0], [5, 5], [0, 300], [-1, 4], [9, 3]):
+        with pytest.raises(ValueError):
+            ihist.edges_table(bad)

@@ -63,3 +63,9 @@ def test_batch_candidates_add_16_bin_groups_for_pixel_major():
     assert not any(t.get("bins_per_cta") == 16 for t in bm)
     assert any(t.get("bins_per_cta") == 16 for t in pm)
     assert len(pm) > len(bm)
+
+
+def test_table_batches_never_try_16_bin_groups():
+    pm = autotune.batch_candidates([(240, 320, 16, 0), (480, 640, 32, 1)], tables=True)
+    assert pm[0] == {}
+    assert not any(t.get("bins_per_cta") == 16 for t in pm)

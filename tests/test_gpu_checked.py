@@ -51,6 +51,19 @@ with ihist.Batch([torch.from_numpy(x).cuda() for x in imgs], [s[2] for s in shap
     assert bt.status() == ihist.IHIST_OK
     for x, o, (h, w, b, l) in zip(imgs, bt.outs, shapes):
         assert np.array_equal(u32(o).reshape(ihist.out_shape(h, w, b, l)), ref_layout(x, b, l)), (h, w, b, l)
+# a table batch: frames with value -> bin tables next to a uniform frame
+edges = [0, 16, 64, 128, 129, 256]
+tabs = [ihist.edges_table(edges), None, [(v * 7) % 9 - 1 for v in range(256)]]
+tshapes = [(270, 480, 5, 0), (64, 257, 7, 1), (100, 1000, 8, 1)]
+timgs = [synth.gradient_frame(60 + i, h, w) for i, (h, w, b, l) in enumerate(tshapes)]
+with ihist.Batch([torch.from_numpy(x).cuda() for x in timgs], [s[2] for s in tshapes], [s[3] for s in tshapes],
+                 tables=tabs) as bt:
+    bt.compute()
+    assert bt.status() == ihist.IHIST_OK
+    for x, o, t, (h, w, b, l) in zip(timgs, bt.outs, tabs, tshapes):
+        r = ref_layout(x, b, 0) if t is None else oracle.integral_histogram_mapped(x, np.asarray(t, np.int32), b)
+        r = r if l == 0 else np.ascontiguousarray(r.transpose(1, 2, 0))
+        assert np.array_equal(u32(o).reshape(ihist.out_shape(h, w, b, l)), r), (h, w, b, l)
 print("checked ok", n)
 '''
 

@@ -1,6 +1,7 @@
-"""Overlapped launches (programmatic dependent launch, tune "overlap": 1):
-back-to-back computes of one plan may run at the same time, each waiting
-for the one before it ahead of its first store.  Results must still equal
+"""Overlapped launches (programmatic dependent launch): every scan and
+query may start while the kernel before it finishes; by default a scan
+waits for it before reading its frame, with tune "overlap": 1 only before
+its first store, so back-to-back computes of one plan run at the same time.  Results must still equal
 the oracle word for word: across many launches (both control-block
 parities), interleaved with queries and other kernels on the stream, in a
 captured graph, after a launch that timed out, and in the host-frame
@@ -170,3 +171,29 @@ def test_joint_and_table_plans_with_overlap():
         assert jp.status() == ihist.IHIST_OK and ep.status() == ihist.IHIST_OK
         assert_same(u32(hj).reshape(jp.out_shape), ref, "joint")
         assert_same(u32(he).reshape(ep.out_shape), ref_e, "edges")
+
+
+def test_default_launch_is_safe_when_the_kernel_before_writes_the_frame():
+    # without overlap=1 a scan reads nothing of its frame before the kernel
+    # launched just before it completed, so a kernel that writes the frame
+    # right before ihist_compute is fine (and so is one that writes the
+    # rectangles right before ihist_query)
+    h, w, nbins = 1080, 1920, 16
+    base = synth.gradient_frame(800, h, w)
+    rects = synth.rects(801, 500, h, w)
+    d = torch.from_numpy(base).cuda()
+    d_r = torch.from_numpy(rects).cuda()
+    d_r2 = torch.empty_like(d_r)
+    with ihist.Plan(h, w, nbins) as plan:
+        out = plan.empty_output()
+        for key in (0x5a, 0x33, 0xff, 0x01):
+            frame = torch.bitwise_xor(d, key)  # an elementwise kernel writes the frame ...
+            plan.compute(frame, out)           # ... and the scan is launched right after it
+            d_r2.copy_(d_r.flip(0))            # a kernel writes the rectangles right before the query
+            rows = plan.query(out, d_r2)
+            torch.cuda.synchronize()
+            img = base ^ key
+            ref = oracle.integral_histogram(img, nbins)
+            assert_same(u32(out).reshape(plan.out_shape), ref, "frame xor %#x" % key)
+            assert np.array_equal(u32(rows), oracle.query(ref, np.ascontiguousarray(rects[::-1])))
+        assert plan.status() == ihist.IHIST_OK
