@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -144,11 +145,10 @@ class ClockSampler:
 
     def __init__(self):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        self.path = os.path.join(tempfile.gettempdir(), "ihist_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
                                           "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
@@ -325,15 +325,20 @@ def configs_report(stream, peak: float) -> dict:
     nbs = [nb for (h, w, nb, sd) in specs]
     byts = sum(h * w * nb * 4 + h * w for (h, w, nb, sd) in specs)
     entry = {"frames": 256, "algorithmic_bytes": byts, "form": "one ihist_batch_compute launch"}
-    for label, tune in (("default", None), ("autotuned", "auto")):
-        with ihist.Batch(fr, nbs, outs=ou, tune=tune) as batch:
+    # the autotuner picks the layout (no queries in this workload) and, for
+    # it, the launch shape
+    auto_layout, auto_tune, layout_ms = autotune.tune_batch_layout([(h, w, nb) for (h, w, nb, sd) in specs], 0)
+    names = {ihist.IHIST_BIN_MAJOR: "bin-major", ihist.IHIST_PIXEL_MAJOR: "pixel-major"}
+    for label, tune, layout in (("default", None, ihist.IHIST_BIN_MAJOR), ("autotuned", auto_tune, auto_layout)):
+        with ihist.Batch(fr, nbs, [layout] * len(fr), outs=ou, tune=tune or None) as batch:
             ms = _median_ms(batch.compute, stream)
             if batch.status() != ihist.IHIST_OK:
                 raise SystemExit("device status error in the uneven batch")
             entry[label] = {"ms": ms, "frames_per_s": 256e3 / ms, "gbs": byts / ms / 1e6,
-                            "frac": byts / ms / 1e6 / peak, "items": batch.items()}
-            if tune == "auto":
-                entry[label]["tune"] = autotune.tune_batch([(h, w, nb, 0) for (h, w, nb, sd) in specs])
+                            "frac": byts / ms / 1e6 / peak, "items": batch.items(), "layout": names[layout]}
+            if label == "autotuned":
+                entry[label]["tune"] = auto_tune
+                entry[label]["layout_ms_while_tuning"] = {names[k]: v for k, v in layout_ms.items()}
                 # the same launch captured once in a CUDA graph and replayed
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g):
@@ -496,10 +501,13 @@ def other_bins_report(d_frames, outs, stream, steps: int = 5) -> dict:
         out[name] = {"frames_per_s": steps * n / sec, "gbs": byts / sec / 1e9,
                      "form": "%d x ihist_compute per step" % n, "tile": plan.tune}
         plan.close()
-    del rgb
-    # the same edges on the same frames in one batched launch (a table batch)
-    with ihist.Batch([d_frames[f] for f in range(n)], NBINS, outs=[outs[f] for f in range(n)],
-                     tables=[ihist.edges_table(edges)] * n) as batch:
+    # the same frames in one batched launch each: the edges as value -> bin
+    # tables, and the joint RGB bins (joint-bin planes, then one scan launch)
+    for name, frames_in, kw, read_bytes in (
+            ("edges_64_nonuniform_batched", [d_frames[f] for f in range(n)],
+             {"tables": [ihist.edges_table(edges)] * n}, H * W),
+            ("joint_rgb_4x4x4_batched", [rgb[f] for f in range(n)], {"joint": [[4, 4, 4]] * n}, 3 * H * W)):
+        batch = ihist.Batch(frames_in, NBINS, outs=[outs[f] for f in range(n)], **kw)
         for _ in range(3):
             batch.compute(stream)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -510,12 +518,14 @@ def other_bins_report(d_frames, outs, stream, steps: int = 5) -> dict:
         b.record(stream)
         torch.cuda.synchronize()
         if batch.status() != ihist.IHIST_OK:
-            raise SystemExit("device status error in the batched edges run")
+            raise SystemExit("device status error in the %s run" % name)
         sec = a.elapsed_time(b) / 1000.0
-        byts = steps * n * (H * W * NBINS * 4 + H * W)
-        out["edges_64_nonuniform_batched"] = {"frames_per_s": steps * n / sec, "gbs": byts / sec / 1e9,
-                                              "form": "one ihist_batch_compute launch over %d frames per step, "
-                                                      "value -> bin tables" % n, "tune": batch.tune}
+        byts = steps * n * (H * W * NBINS * 4 + read_bytes)
+        out[name] = {"frames_per_s": steps * n / sec, "gbs": byts / sec / 1e9,
+                     "form": "ihist_batch_compute over %d frames per step (%s)" % (n, ", ".join(kw)),
+                     "tune": batch.tune}
+        batch.close()
+    del rgb
     return out
 
 

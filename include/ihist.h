@@ -289,13 +289,23 @@ typedef struct ihist_batch_s *ihist_batch_t;
  * bin_of_value: NULL for uniform bins, or a HOST array of 256 ints as for
  * ihist_plan_lut (bin of each intensity in [0, nbins), -1 = no bin; bins by
  * edges are such a table), read during ihist_batch_plan / ihist_batch_set_io
- * and copied into the batch. */
+ * and copied into the batch.
+ * channels: 0 or 1 for one byte per pixel; 2..4 for a joint-bin frame as
+ * for ihist_plan_joint: d_in holds `channels` interleaved bytes per pixel
+ * (in_pitch >= w * channels), channel c is cut into bins_per_channel[c]
+ * uniform bins (channel 0 the most significant digit) and nbins must equal
+ * their product; bin_of_value must then be NULL.  The batch computes each
+ * joint frame's joint-bin plane (one byte per pixel, in its workspace) just
+ * before the scan.  A zero-initialised struct is a uniform one-channel
+ * frame. */
 typedef struct {
   int h, w, nbins, layout;
   const uint8_t *d_in;
   size_t in_pitch;
   uint32_t *d_out;
   const int *bin_of_value;
+  int channels;
+  int bins_per_channel[4];
 } ihist_frame_t;
 
 /* Plan a batch of n >= 1 frames (limits per frame as for ihist_plan); the
@@ -353,7 +363,8 @@ int ihist_batch_query_all(ihist_batch_t batch, const int32_t *d_rects, int n, ui
                           void *stream);
 
 /* Upload every frame of the batch from page-locked HOST memory on
- * copy_stream (h_frames[i]: h x w bytes, rows packed) into the batch's
+ * copy_stream (h_frames[i]: h x w bytes, rows packed; w * channels bytes
+ * per row for a joint frame) into the batch's
  * device inputs, then compute the batch on `stream` once the copies land
  * (Algorithm 6's dual buffering, one batch at a time).  Two batches driven
  * alternately overlap one batch's upload with the other's compute.  The

@@ -7,8 +7,9 @@ warps per CTA).  Each candidate is
 timed with CUDA events on a seeded uniform frame (median of a few launches
 after warm-up); candidates the library rejects (shared memory, registers)
 are skipped.  For a batch the search covers R and G of the batched launch.
-``choose_layout`` times compute plus a query load for bin-major and
-pixel-major output and keeps the faster, for callers that accept either.
+``choose_layout`` (one frame) and ``tune_batch_layout`` (a batch) time
+compute plus a query load for bin-major and pixel-major output and keep the
+faster, for callers that accept either.
 
 Results are cached in a JSON file (``IHIST_TUNE_CACHE`` or
 ``~/.cache/ihist_tune.json``) keyed by device name and shape.  The timing
@@ -102,20 +103,34 @@ def time_plan(h, w, nbins, layout, tune, reps=5):
     return statistics.median(ms)
 
 
-def time_batch(shapes, tune, reps=3, tables=False):
+def time_batch(shapes, tune, reps=3, tables=False, queries=0):
     """Median ms of one batched launch over frames of these (h, w, nbins,
-    layout); tables: every frame bins through a value -> bin table."""
+    layout), plus one batched query launch of `queries` rectangles per frame;
+    tables: every frame bins through a value -> bin table."""
     import torch
     frames = [torch.from_numpy(synth.uniform_frame(100 + i, h, w)).cuda() for i, (h, w, b, l) in enumerate(shapes)]
     tb = [[(v * s[2]) >> 8 for v in range(256)] for s in shapes] if tables else None
+    rects = None
+    if queries:
+        import numpy as np
+        rects = torch.from_numpy(np.stack([synth.rects(200 + i, queries, h, w)
+                                           for i, (h, w, b, l) in enumerate(shapes)])).cuda()  # [frames][n][4]
     with ihist.Batch(frames, [s[2] for s in shapes], [s[3] for s in shapes], tune=tune or None, tables=tb) as batch:
-        for _ in range(2):
+        qout = (torch.empty((queries * sum(s[2] for s in shapes),), dtype=torch.int32, device="cuda")
+                if queries else None)
+
+        def step():
             batch.compute()
+            if queries:
+                batch.query_all(rects, out=qout)
+
+        for _ in range(2):
+            step()
         ms = []
         for _ in range(reps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            batch.compute()
+            step()
             b.record()
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
@@ -177,6 +192,30 @@ def tune_batch(shapes, timer=None, device=None, use_cache=True, tables=False):
             cache[key] = {"tune": best, "ms": ms}
             _store_cache(path, cache)
     return best
+
+
+def tune_batch_layout(shapes, queries_per_frame=0, timer=None, device=None, use_cache=True):
+    """Layout and launch shape of a batch of (h, w, nbins) frames that are
+    computed once and then queried `queries_per_frame` times each.  For each
+    layout (the same for every frame) the launch shape comes from
+    tune_batch; the layout whose batched launch plus batched queries take
+    less time wins.  timer(shapes, tune, queries) -> ms replaces the
+    measurement (tests).  Returns (layout, tune, {layout: ms})."""
+    device = device or _device_key()
+    times, tunes = {}, {}
+    for layout in (ihist.IHIST_BIN_MAJOR, ihist.IHIST_PIXEL_MAJOR):
+        sh = [(h, w, b, layout) for (h, w, b) in shapes]
+        shape_timer = None if timer is None else (lambda t, sh=sh: timer(sh, t, 0))
+        try:
+            tunes[layout] = tune_batch(sh, timer=shape_timer, device=device, use_cache=use_cache)
+        except RuntimeError:
+            continue  # no launch shape runs this layout
+        times[layout] = (timer(sh, tunes[layout], queries_per_frame) if timer is not None
+                         else time_batch(sh, tunes[layout], queries=queries_per_frame))
+    if not times:
+        raise RuntimeError("no layout ran")
+    layout = min(times, key=times.get)
+    return layout, tunes[layout], times
 
 
 def choose_layout(h, w, nbins, queries_per_frame=1000, timer=None):

@@ -365,26 +365,51 @@ extern "C" int ihist_plan_edges(int h, int w, int nbins, int layout, const int *
   return ihist_plan_lut(h, w, nbins, layout, table, tune, out);
 }
 
-extern "C" int ihist_plan_joint(int h, int w, int channels, const int *bins_per_channel, int layout,
-                                const ihist_tune_t *tune, ihist_plan_t *out) {
+int ihist::host::joint_bin_count(int channels, const int *bins_per_channel, int *nbins) {
   if (channels < 1 || channels > 4 || !bins_per_channel) return IHIST_ERR_INVALID_ARG;
+  long long n = 1;
+  for (int c = 0; c < channels; ++c) {
+    if (bins_per_channel[c] < 1 || bins_per_channel[c] > 256) return IHIST_ERR_INVALID_ARG;
+    n *= bins_per_channel[c];
+    if (n > 256) return IHIST_ERR_UNSUPPORTED;
+  }
+  *nbins = (int)n;
+  return IHIST_OK;
+}
+
+// Digit weights of the joint bin: channel 0 most significant.
+static JointBins joint_bins(int channels, const int *bins_per_channel) {
   JointBins jb;
   std::memset(&jb, 0, sizeof(jb));
   jb.C = channels;
-  long long nbins = 1;
-  for (int c = 0; c < channels; ++c) {
-    if (bins_per_channel[c] < 1 || bins_per_channel[c] > 256) return IHIST_ERR_INVALID_ARG;
-    jb.mul[c] = bins_per_channel[c];
-    nbins *= bins_per_channel[c];
-    if (nbins > 256) return IHIST_ERR_UNSUPPORTED;
-  }
+  for (int c = 0; c < channels; ++c) jb.mul[c] = bins_per_channel[c];
   int stride = 1;
   for (int c = channels - 1; c >= 0; --c) {
     jb.stride[c] = stride;
     stride *= jb.mul[c];
   }
+  return jb;
+}
+
+int ihist::host::launch_joint_index(const uint8_t *in, long long pitch, int H, int W, int channels,
+                                    const int *bins_per_channel, uint8_t *idx, long long idx_pitch, int sms,
+                                    void *stream) {
+  const JointBins jb = joint_bins(channels, bins_per_channel);
+  const unsigned long long quads = (unsigned long long)H * (((unsigned)W + 3u) / 4u);
+  const unsigned int grid =
+      (unsigned int)std::min<unsigned long long>((quads + 255) / 256, (unsigned long long)sms * 8ull);
+  joint_index_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(in, pitch, H, W, jb, idx, idx_pitch);
+  return cudaGetLastError() == cudaSuccess ? IHIST_OK : IHIST_ERR_CUDA;
+}
+
+extern "C" int ihist_plan_joint(int h, int w, int channels, const int *bins_per_channel, int layout,
+                                const ihist_tune_t *tune, ihist_plan_t *out) {
+  int nbins = 0;
+  const int rc = joint_bin_count(channels, bins_per_channel, &nbins);
+  if (rc != IHIST_OK) return rc;
   if ((long long)w * channels > 65535) return IHIST_ERR_UNSUPPORTED;
-  return plan_create(h, w, (int)nbins, layout, tune, nullptr, &jb, out);
+  const JointBins jb = joint_bins(channels, bins_per_channel);
+  return plan_create(h, w, nbins, layout, tune, nullptr, &jb, out);
 }
 
 extern "C" int ihist_plan_channels(ihist_plan_t p) {
@@ -456,12 +481,9 @@ static int compute_frame(ihist_plan_s *p, const uint8_t *d_in, size_t in_pitch, 
   if (rc != IHIST_OK) return rc;
   if (p->binning == kJoint) {
     // joint bins first, one byte per pixel; the scan then reads that plane
-    const unsigned long long quads = (unsigned long long)p->H * (((unsigned)p->W + 3u) / 4u);
-    const unsigned int grid = (unsigned int)std::min<unsigned long long>((quads + 255) / 256,
-                                                                         (unsigned long long)p->sms * 8ull);
-    joint_index_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_in, (long long)in_pitch, p->H, p->W, p->joint,
-                                                                p->idx, (long long)p->idx_pitch);
-    if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
+    int rc2 = launch_joint_index(d_in, (long long)in_pitch, p->H, p->W, p->joint.C, p->joint.mul, p->idx,
+                                 (long long)p->idx_pitch, p->sms, stream);
+    if (rc2 != IHIST_OK) return rc2;
     d_in = p->idx;
     in_pitch = p->idx_pitch;
     overlap = false;  // the scan reads the plane the kernel just launched writes

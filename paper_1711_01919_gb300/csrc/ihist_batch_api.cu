@@ -80,7 +80,31 @@ bool batch_frame_tiling(int h, int w, int nbins, int layout, int G, int R_req, i
 
 size_t frame_nci(const FrameDesc &f) { return (size_t)f.nbands * f.ngroups * f.nchunks; }
 
+// Joint-bin frames (2..4 interleaved channels): the scan reads the frame's
+// joint-bin plane, which the batch computes into its workspace (rows
+// idx_pitch bytes) just before the scan.
+bool frame_joint(const ihist_frame_t &fr) { return fr.channels >= 2; }
+int frame_channels(const ihist_frame_t &fr) { return frame_joint(fr) ? fr.channels : 1; }
+size_t idx_pitch_of(int w) { return align_up((size_t)w, 16); }
+size_t idx_bytes_of(const ihist_frame_t &fr) {
+  return frame_joint(fr) ? (size_t)fr.h * idx_pitch_of(fr.w) : 0;
+}
+
+// A joint frame's channels and bins follow ihist_plan_joint's rules, its
+// bins multiply to nbins and it has no value -> bin table.
+int joint_ok(const ihist_frame_t &fr) {
+  if (fr.channels < 0 || fr.channels > 4) return IHIST_ERR_INVALID_ARG;
+  if (!frame_joint(fr)) return IHIST_OK;
+  int nb = 0;
+  const int rc = joint_bin_count(fr.channels, fr.bins_per_channel, &nb);
+  if (rc != IHIST_OK) return rc;
+  if (nb != fr.nbins || fr.bin_of_value) return IHIST_ERR_INVALID_ARG;
+  if ((long long)fr.w * fr.channels > 65535) return IHIST_ERR_UNSUPPORTED;
+  return IHIST_OK;
+}
+
 bool frame_tma_ok(const ihist_frame_t &fr) {
+  if (frame_joint(fr)) return fr.w >= kChunk;  // the plane is 16-byte aligned, pitch a multiple of 16
   return !((uintptr_t)fr.d_in & 15u) && !(fr.in_pitch & 15u) && fr.w >= kChunk &&
          fr.in_pitch < (1ull << 40);
 }
@@ -99,11 +123,14 @@ bool table_ok(const ihist_frame_t &fr) {
 }
 
 // The kernel's form of a frame's binning: 8 * bin of each value, or kNoBin;
-// uniform frames of a table batch get the table of q = floor(v * B / 256).
+// uniform frames of a table batch get the table of q = floor(v * B / 256),
+// joint frames the identity on their joint-bin plane.
 void fill_table(const ihist_frame_t &fr, uint32_t *dst) {
   for (int v = 0; v < 256; ++v) {
     if (fr.bin_of_value)
       dst[v] = fr.bin_of_value[v] >= 0 ? 8u * (uint32_t)fr.bin_of_value[v] : kNoBin;
+    else if (frame_joint(fr))
+      dst[v] = v < fr.nbins ? 8u * (uint32_t)v : kNoBin;
     else
       dst[v] = 8u * (((uint32_t)v * (uint32_t)fr.nbins) >> 8);
   }
@@ -128,6 +155,8 @@ struct ihist_batch_s {
   uint32_t *d_lut;                                    // table batches: [slot][256]
   std::vector<size_t> slot_nci;                       // carry capacity of each slot
   std::vector<uint32_t *> slot_flags, slot_cnt, slot_left, slot_incl;
+  std::vector<size_t> slot_idx_cap;                   // joint-bin plane bytes of each slot
+  std::vector<uint8_t *> slot_idx;
   std::vector<FrameDesc> fd;                          // current frames
   std::vector<ihist_frame_t> io;
   FrameDesc *h_fd;           // pinned staging
@@ -139,14 +168,15 @@ struct ihist_batch_s {
   bool launched;
 };
 
-static bool encode_frame_map(const ihist_frame_t &fr, int R, CUtensorMap *map) {
+// TMA descriptor of the plane the scan reads (the frame, or its joint-bin plane).
+static bool encode_frame_map(const uint8_t *in, size_t pitch, int h, int w, int R, CUtensorMap *map) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
-  cuuint64_t gdim[2] = {(cuuint64_t)fr.w, (cuuint64_t)fr.h};
-  cuuint64_t gstride[1] = {(cuuint64_t)fr.in_pitch};
+  cuuint64_t gdim[2] = {(cuuint64_t)w, (cuuint64_t)h};
+  cuuint64_t gstride[1] = {(cuuint64_t)pitch};
   cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)R};
   cuuint32_t estride[2] = {1u, 1u};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(fr.d_in), gdim, gstride,
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(in), gdim, gstride,
              box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -163,18 +193,22 @@ static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames, int n) {
     const ihist_frame_t &fr = frames[i];
     int rc = validate_shape(fr.h, fr.w, fr.nbins, fr.layout);
     if (rc != IHIST_OK) return rc;
-    if (!fr.d_in || !fr.d_out || fr.in_pitch < (size_t)fr.w || ((uintptr_t)fr.d_out & 3u) ||
+    rc = joint_ok(fr);
+    if (rc != IHIST_OK) return rc;
+    if (!fr.d_in || !fr.d_out || fr.in_pitch < (size_t)fr.w * frame_channels(fr) || ((uintptr_t)fr.d_out & 3u) ||
         fr.in_pitch > (size_t)LLONG_MAX || !table_ok(fr))
       return IHIST_ERR_INVALID_ARG;
     if (fr.bin_of_value && !b->lut) return IHIST_ERR_UNSUPPORTED;  // planned without tables
+    if (idx_bytes_of(fr) > b->slot_idx_cap[i]) return IHIST_ERR_UNSUPPORTED;  // no joint-bin plane that large
     FrameDesc &f = fd[i];
     if (!batch_frame_tiling(fr.h, fr.w, fr.nbins, fr.layout, b->G, b->R_req, b->mmax, b->ncg_max, b->warps,
                             &f) ||
         frame_nci(f) > b->slot_nci[i] || f.R > b->R_max || f.nchunks * f.gpc > b->ncg_max ||
         mmax_for(f.m) > b->mmax)
       return IHIST_ERR_UNSUPPORTED;  // does not fit the slot planned for it
-    f.in = fr.d_in;
-    f.pitch = (long long)fr.in_pitch;
+    f.in = frame_joint(fr) ? b->slot_idx[i] : fr.d_in;
+    f.pitch = frame_joint(fr) ? (long long)idx_pitch_of(fr.w) : (long long)fr.in_pitch;
+    if (frame_joint(fr)) f.qmul = 256;  // the plane holds bin indices
     f.out = fr.d_out;
     f.flags = b->slot_flags[i];
     f.agg_cnt = b->slot_cnt[i];
@@ -189,7 +223,8 @@ static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames, int n) {
   if (total >= 0xffffffffull) return IHIST_ERR_UNSUPPORTED;
   for (int i = 0; i < n; ++i) {
     if (tma) {
-      if (!encode_frame_map(frames[i], fd[i].R, &b->h_tm[i])) return IHIST_ERR_CUDA;
+      if (!encode_frame_map(fd[i].in, (size_t)fd[i].pitch, frames[i].h, frames[i].w, fd[i].R, &b->h_tm[i]))
+        return IHIST_ERR_CUDA;
     } else {
       std::memset(&b->h_tm[i], 0, sizeof(CUtensorMap));
     }
@@ -277,7 +312,9 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   if (t.warps_per_cta != 0 && t.warps_per_cta != 4 && t.warps_per_cta != 8 && t.warps_per_cta != 16)
     return IHIST_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
-    const int rc = validate_shape(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout);
+    int rc = validate_shape(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout);
+    if (rc != IHIST_OK) return rc;
+    rc = joint_ok(frames[i]);
     if (rc != IHIST_OK) return rc;
     if (!table_ok(frames[i])) return IHIST_ERR_INVALID_ARG;
   }
@@ -438,6 +475,11 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
     off = align_up(off + nci * b->G * 4, 256);
     off = align_up(off + nci * b->G * kChunk * 4, 256);
   }
+  const size_t o_idx = off;  // joint-bin planes of the slots planned with joint frames
+  for (int i = 0; i < n; ++i) {
+    b->slot_idx_cap.push_back(idx_bytes_of(frames[i]));
+    off = align_up(off + b->slot_idx_cap[i], 256);
+  }
   b->ws_bytes = off;
   if (cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess ||
       cudaMallocHost((void **)&b->h_fd, (size_t)n * sizeof(FrameDesc)) != cudaSuccess ||
@@ -470,6 +512,11 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
     co = align_up(co + nci * b->G * 4, 256);
     b->slot_incl.push_back(reinterpret_cast<uint32_t *>(base + co));
     co = align_up(co + nci * b->G * kChunk * 4, 256);
+  }
+  size_t xo = o_idx;
+  for (int i = 0; i < n; ++i) {
+    b->slot_idx.push_back(b->slot_idx_cap[i] ? reinterpret_cast<uint8_t *>(base + xo) : nullptr);
+    xo = align_up(xo + b->slot_idx_cap[i], 256);
   }
   int rc = batch_bind(b, frames, n);
   if (rc != IHIST_OK) {
@@ -524,6 +571,14 @@ extern "C" int ihist_batch_compute(ihist_batch_t b, void *stream) {
   if (!b) return IHIST_ERR_INVALID_ARG;
   int rc = check_batch_device(b);
   if (rc != IHIST_OK) return rc;
+  // joint frames: their joint-bin planes first (the scan waits for them)
+  for (int i = 0; i < b->n; ++i) {
+    const ihist_frame_t &fr = b->io[i];
+    if (!frame_joint(fr)) continue;
+    rc = launch_joint_index(fr.d_in, (long long)fr.in_pitch, fr.h, fr.w, fr.channels, fr.bins_per_channel,
+                            b->slot_idx[i], (long long)idx_pitch_of(fr.w), b->sms, stream);
+    if (rc != IHIST_OK) return rc;
+  }
   BatchFn fn = batch_fn(b->G, b->mmax, b->tma, b->vec, b->lut);
   const int cps = b->ctas_per_sm[b->tma ? 1 : 0][b->vec ? 1 : 0];
   const unsigned int grid = std::min<unsigned int>(b->total, (unsigned int)(cps * b->sms));
@@ -548,8 +603,9 @@ extern "C" int ihist_batch_upload_compute(ihist_batch_t b, const uint8_t *const 
   if (b->launched && cudaStreamWaitEvent(cs, b->computed, 0) != cudaSuccess) return IHIST_ERR_CUDA;
   for (int i = 0; i < b->n; ++i) {
     const ihist_frame_t &fr = b->io[i];
-    if (cudaMemcpy2DAsync(const_cast<uint8_t *>(fr.d_in), fr.in_pitch, h_frames[i], (size_t)fr.w,
-                          (size_t)fr.w, (size_t)fr.h, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+    const size_t row = (size_t)fr.w * frame_channels(fr);
+    if (cudaMemcpy2DAsync(const_cast<uint8_t *>(fr.d_in), fr.in_pitch, h_frames[i], row, row, (size_t)fr.h,
+                          cudaMemcpyHostToDevice, cs) != cudaSuccess)
       return IHIST_ERR_CUDA;
   }
   if (cudaEventRecord(b->uploaded, cs) != cudaSuccess ||

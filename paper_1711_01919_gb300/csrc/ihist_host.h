@@ -32,6 +32,16 @@ int validate_shape(int h, int w, int nbins, int layout);
 int launch_query(int H, int W, int B, int layout, int sms, Ctrl *ctrl, const uint32_t *d_hist,
                  const int32_t *d_rects, int n, uint32_t *d_hist_out, void *stream);
 
+// Joint bins of C interleaved channels (ihist_plan_joint's rules):
+// IHIST_OK and the joint bin count in *nbins, or the error code.
+int joint_bin_count(int channels, const int *bins_per_channel, int *nbins);
+
+// The joint-bin plane of one multi-channel frame (one byte per pixel,
+// rows idx_pitch bytes, a multiple of 16) on `stream`.
+int launch_joint_index(const uint8_t *in, long long pitch, int H, int W, int channels,
+                       const int *bins_per_channel, uint8_t *idx, long long idx_pitch, int sms,
+                       void *stream);
+
 // Synchronise `stream`, read and clear the device status word.
 int read_status(Ctrl *ctrl, void *stream, int *device_status);
 

@@ -74,6 +74,8 @@ class ihist_frame_t(ctypes.Structure):
         ("in_pitch", ctypes.c_size_t),
         ("d_out", ctypes.c_void_p),
         ("bin_of_value", ctypes.POINTER(ctypes.c_int)),
+        ("channels", ctypes.c_int),
+        ("bins_per_channel", ctypes.c_int * 4),
     ]
 
 
@@ -324,12 +326,18 @@ def _table_ptr(table):
 
 
 def _frames_array(frames):
-    """frames: (h, w, nbins, layout, d_in, in_pitch, d_out[, table]) tuples."""
+    """frames: (h, w, nbins, layout, d_in, in_pitch, d_out[, table[,
+    bins_per_channel]]) tuples; bins_per_channel (2..4 entries) makes a
+    joint-bin frame of that many interleaved channels."""
     arr = (ihist_frame_t * len(frames))()
     for i, fr in enumerate(frames):
         h, w, nbins, layout, d_in, pitch, d_out = fr[:7]
         table = fr[7] if len(fr) > 7 else None
-        arr[i] = ihist_frame_t(h, w, nbins, layout, d_in, pitch, d_out, _table_ptr(table))
+        joint = list(fr[8]) if len(fr) > 8 and fr[8] is not None else []
+        if len(joint) > 4:
+            raise ValueError("at most 4 channels")
+        arr[i] = ihist_frame_t(h, w, nbins, layout, d_in, pitch, d_out, _table_ptr(table), len(joint),
+                               (ctypes.c_int * 4)(*(joint + [0] * (4 - len(joint)))))
     return arr
 
 
@@ -556,9 +564,11 @@ class Batch:
     """Many frames (CUDA uint8 [h][w] tensors, any mix of shapes) in one
     persistent launch; outputs are int32 tensors holding uint32 counts."""
 
-    def __init__(self, frames, nbins, layouts=None, outs=None, tune=None, tables=None):
+    def __init__(self, frames, nbins, layouts=None, outs=None, tune=None, tables=None, joint=None):
         """tables: None, or one entry per frame, None (uniform bins) or a
-        256-entry value -> bin table (see edges_table)."""
+        256-entry value -> bin table (see edges_table).  joint: None, or one
+        entry per frame, None or the bins of each channel of a joint-bin
+        frame ([h][w][C] uint8 tensor, nbins = their product)."""
         import torch
         n = len(frames)
         nb = list(nbins) if hasattr(nbins, "__len__") else [nbins] * n
@@ -566,6 +576,7 @@ class Batch:
         self.frames = list(frames)
         self.nbins, self.layouts = nb, ly
         self.tables = list(tables) if tables is not None else [None] * n
+        self.joint = list(joint) if joint is not None else [None] * n
         self.outs = list(outs) if outs is not None else [
             torch.empty(out_shape(f.shape[0], f.shape[1], b, l), dtype=torch.int32, device=f.device)
             for f, b, l in zip(self.frames, nb, ly)]
@@ -578,25 +589,31 @@ class Batch:
 
     def _desc(self):
         d = []
-        for f, b, l, o, t in zip(self.frames, self.nbins, self.layouts, self.outs, self.tables):
-            if f.dtype.itemsize != 1 or f.dim() != 2 or f.stride(1) != 1:
+        for f, b, l, o, t, j in zip(self.frames, self.nbins, self.layouts, self.outs, self.tables, self.joint):
+            if j is not None:
+                if (f.dtype.itemsize != 1 or f.dim() != 3 or f.shape[2] != len(j) or f.stride(2) != 1
+                        or f.stride(1) != len(j)):
+                    raise ValueError("joint frames must be uint8 [h][w][C] tensors with interleaved channels")
+            elif f.dtype.itemsize != 1 or f.dim() != 2 or f.stride(1) != 1:
                 raise ValueError("frames must be 2-D uint8 tensors with unit column stride")
-            d.append((f.shape[0], f.shape[1], b, l, f.data_ptr(), f.stride(0), o.data_ptr(), t))
+            d.append((f.shape[0], f.shape[1], b, l, f.data_ptr(), f.stride(0), o.data_ptr(), t, j))
         return d
 
-    def set_io(self, frames, outs, nbins=None, layouts=None, stream=None, tables=None):
+    def set_io(self, frames, outs, nbins=None, layouts=None, stream=None, tables=None, joint=None):
         """Bind new frames/outputs (any shapes that fit the planned slots);
-        tables as for the constructor (default: uniform bins)."""
+        tables and joint as for the constructor (default: uniform bins of
+        one-channel frames)."""
         frames, outs = list(frames), list(outs)
         nb = list(nbins) if nbins is not None else self.nbins[:len(frames)]
         ly = list(layouts) if layouts is not None else self.layouts[:len(frames)]
         tb = list(tables) if tables is not None else [None] * len(frames)
-        old = (self.frames, self.outs, self.nbins, self.layouts, self.tables)
-        self.frames, self.outs, self.nbins, self.layouts, self.tables = frames, outs, nb, ly, tb
+        jt = list(joint) if joint is not None else [None] * len(frames)
+        old = (self.frames, self.outs, self.nbins, self.layouts, self.tables, self.joint)
+        self.frames, self.outs, self.nbins, self.layouts, self.tables, self.joint = frames, outs, nb, ly, tb, jt
         try:
             ihist_batch_set_io(self.handle, self._desc(), _stream(stream))
         except Exception:
-            self.frames, self.outs, self.nbins, self.layouts, self.tables = old
+            self.frames, self.outs, self.nbins, self.layouts, self.tables, self.joint = old
             raise
 
     def compute(self, stream=None):

@@ -139,3 +139,17 @@ def test_edges_table_matches_the_oracle_binning():
     for bad in ([0], [5, 5], [0, 300], [-1, 4], [9, 3]):
         with pytest.raises(ValueError):
             ihist.edges_table(bad)
+
+
+def test_batch_joint_frames_are_checked_before_touching_cuda(lib):
+    # (h, w, nbins, layout, d_in, in_pitch, d_out, table, bins_per_channel)
+    good = [4, 4]
+    for fr, code in (((16, 16, 15, 0, 16, 64, 16, None, good), ihist.IHIST_ERR_INVALID_ARG),   # 4 x 4 != 15
+                     ((16, 16, 16, 0, 16, 64, 16, [0] * 256, good), ihist.IHIST_ERR_INVALID_ARG),  # joint + table
+                     ((16, 16, 0, 0, 16, 64, 16, None, [0, 4]), ihist.IHIST_ERR_INVALID_ARG),
+                     ((16, 16, 256, 0, 16, 64, 16, None, [32, 16]), ihist.IHIST_ERR_UNSUPPORTED)):   # 512 bins
+        with pytest.raises(ihist.IhistError) as e:
+            ihist.ihist_batch_plan([fr])
+        assert e.value.code == code, fr
+    with pytest.raises(ValueError):
+        ihist.ihist_batch_plan([(16, 16, 32, 0, 16, 64, 16, None, [2, 2, 2, 2, 2])])

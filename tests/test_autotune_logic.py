@@ -69,3 +69,25 @@ def test_table_batches_never_try_16_bin_groups():
     pm = autotune.batch_candidates([(240, 320, 16, 0), (480, 640, 32, 1)], tables=True)
     assert pm[0] == {}
     assert not any(t.get("bins_per_cta") == 16 for t in pm)
+
+
+def test_batch_layout_takes_the_faster_layout_with_its_own_launch_shape(tmp_path, monkeypatch):
+    monkeypatch.setenv("IHIST_TUNE_CACHE", str(tmp_path / "cache.json"))
+    shapes = [(240, 320, 16), (1080, 1920, 64)]
+    seen = []
+
+    def timer(sh, tune, queries):
+        layout = sh[0][3]
+        assert all(s[3] == layout for s in sh)
+        seen.append((layout, queries))
+        # pixel-major: slower to compute, faster to query
+        base = 5.0 if layout == ihist.IHIST_BIN_MAJOR else 8.0
+        per_query = 0.004 if layout == ihist.IHIST_BIN_MAJOR else 0.001
+        return base + per_query * queries + (0.0 if tune == {} else 0.5)
+
+    layout, tune, times = autotune.tune_batch_layout(shapes, 0, timer=timer, device="fake")
+    assert layout == ihist.IHIST_BIN_MAJOR and tune == {}
+    assert times[ihist.IHIST_BIN_MAJOR] == 5.0 and times[ihist.IHIST_PIXEL_MAJOR] == 8.0
+    layout, tune, times = autotune.tune_batch_layout(shapes, 2000, timer=timer, device="fake")
+    assert layout == ihist.IHIST_PIXEL_MAJOR  # 8 + 2 < 5 + 8
+    assert (ihist.IHIST_PIXEL_MAJOR, 2000) in seen

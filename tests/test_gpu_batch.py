@@ -236,3 +236,21 @@ def test_pixel_major_batch_defaults_to_16_bin_groups():
         batch.compute()
         assert batch.status() == ihist.IHIST_OK
         check_batch(batch, imgs, nbins, [1] * len(shapes))
+
+
+def test_autotuned_layout_and_launch_shape_give_exact_batches(tmp_path, monkeypatch):
+    # the autotuner times both layouts (each with its own tuned launch shape)
+    # with and without a query load; whatever it picks computes exactly
+    from paper_1711_01919_gb300 import autotune
+    monkeypatch.setenv("IHIST_TUNE_CACHE", str(tmp_path / "tune.json"))
+    shapes = [(240, 320, 16), (480, 640, 32), (100, 1000, 8)]
+    imgs = [synth.uniform_frame(70 + i, h, w) for i, (h, w, b) in enumerate(shapes)]
+    nbins = [b for (h, w, b) in shapes]
+    for queries in (0, 4000):
+        layout, tune, times = autotune.tune_batch_layout(shapes, queries, use_cache=False)
+        assert set(times) == {ihist.IHIST_BIN_MAJOR, ihist.IHIST_PIXEL_MAJOR}
+        assert times[layout] == min(times.values())
+        with ihist.Batch([torch.from_numpy(x).cuda() for x in imgs], nbins, [layout] * 3, tune=tune or None) as batch:
+            batch.compute()
+            assert batch.status() == ihist.IHIST_OK
+            check_batch(batch, imgs, nbins, [layout] * 3)

@@ -154,3 +154,66 @@ def test_upload_compute_with_tables():
         torch.cuda.synchronize()
         assert batch.status() == ihist.IHIST_OK
         check(batch, imgs, nbins, tables, layouts)
+
+
+def joint_frame(seed, h, w, c):
+    return np.ascontiguousarray(np.stack([synth.uniform_frame(seed + k, h, w) for k in range(c)], axis=2))
+
+
+JOINT_CASES = [  # (h, w, bins per channel, layout)
+    (150, 300, [4, 4, 4], 0), (64, 257, [8, 2], 1), (37, 131, [2, 2, 2, 2], 0), (240, 320, [16, 16], 0),
+    (1, 5, [3, 5], 1), (200, 700, [5], None)]
+
+
+@pytest.mark.parametrize("with_tables", [False, True])
+def test_joint_frames_next_to_uniform_and_table_frames(with_tables):
+    frames, nbins, layouts, tables, joint, refs = [], [], [], [], [], []
+    for i, (h, w, bins, l) in enumerate(JOINT_CASES):
+        if l is None:  # a one-channel frame between the joint ones
+            img = synth.gradient_frame(1200 + i, h, w)
+            t = random_table(1200 + i, bins[0]) if with_tables else None
+            frames.append(img), nbins.append(bins[0]), layouts.append(0), tables.append(t), joint.append(None)
+            refs.append(reference(img, bins[0], t, 0))
+            continue
+        img = joint_frame(1200 + 10 * i, h, w, len(bins))
+        nb = int(np.prod(bins))
+        frames.append(img), nbins.append(nb), layouts.append(l), tables.append(None), joint.append(bins)
+        ref = oracle.integral_histogram_joint(img, bins)
+        refs.append(ref if l == 0 else np.ascontiguousarray(ref.transpose(1, 2, 0)))
+    with ihist.Batch([torch.from_numpy(x).cuda() for x in frames], nbins, layouts, tables=tables,
+                     joint=joint) as batch:
+        for _ in range(2):  # the joint-bin planes are recomputed each launch
+            batch.compute()
+        assert batch.status() == ihist.IHIST_OK
+        for i, (img, b, l) in enumerate(zip(frames, nbins, layouts)):
+            got = u32(batch.outs[i]).reshape(ihist.out_shape(img.shape[0], img.shape[1], b, l))
+            assert np.array_equal(got, refs[i]), "frame %d" % i
+        # joint frames computed alone through joint plans give the same words
+        h, w, bins, l = JOINT_CASES[0]
+        with ihist.Plan(h, w, bins_per_channel=bins) as plan:
+            assert torch.equal(plan.compute(torch.from_numpy(frames[0]).cuda()), batch.outs[0])
+
+
+def test_joint_frames_rebind_and_upload():
+    shapes = [(120, 400, [4, 4, 4]), (90, 640, [8, 4])]
+    imgs = [joint_frame(1300 + 10 * i, h, w, len(b)) for i, (h, w, b) in enumerate(shapes)]
+    nbins = [int(np.prod(b)) for (h, w, b) in shapes]
+    joint = [b for (h, w, b) in shapes]
+    d = [torch.from_numpy(x).cuda() for x in imgs]
+    with ihist.Batch(d, nbins, joint=joint) as batch:
+        # new joint frames of the same shapes, uploaded from pinned host memory
+        imgs2 = [joint_frame(1400 + 10 * i, h, w, len(b)) for i, (h, w, b) in enumerate(shapes)]
+        batch.set_io(d, batch.outs, nbins=nbins, joint=joint)
+        s, cs = torch.cuda.Stream(), torch.cuda.Stream()
+        batch.upload_compute([torch.from_numpy(x).pin_memory() for x in imgs2], stream=s, copy_stream=cs)
+        torch.cuda.synchronize()
+        assert batch.status() == ihist.IHIST_OK
+        for i, (h, w, b) in enumerate(shapes):
+            got = u32(batch.outs[i]).reshape(nbins[i], h, w)
+            assert np.array_equal(got, oracle.integral_histogram_joint(imgs2[i], b)), "frame %d" % i
+        # a slot planned for a one-channel frame has no joint-bin plane
+    with ihist.Batch([torch.from_numpy(synth.uniform_frame(5, 64, 256)).cuda()], [16]) as batch:
+        with pytest.raises(ihist.IhistError) as e:
+            batch.set_io([torch.from_numpy(joint_frame(6, 64, 256, 2)).cuda()], batch.outs, nbins=[16],
+                         joint=[[4, 4]])
+        assert e.value.code == ihist.IHIST_ERR_UNSUPPORTED

@@ -2,15 +2,23 @@
 launch configuration the bench uses.
 
 Checks: sampled bin planes word for word against the oracle (each plane is
-an independent run of Algorithm 1); every word through the second-difference
+an independent run of Algorithm 1), and every one of the 128 planes against
+the oracle's by SHA-256 digest (the planes computed in parallel on the host
+cores); every word through the second-difference
 property (Algorithm 1 solved for Q: the 2-D second difference of H is the
 one-hot of the pixel's bin); 2^20 region queries against the oracle's Eq. 2 on
 the sampled planes, and per-rectangle totals equal to the rectangle's area.
 """
+import concurrent.futures as cf
+import hashlib
+import multiprocessing
+import os
+
 import numpy as np
 import pytest
 
 import oracle
+import oracle_planes
 from paper_1711_01919_gb300 import ihist, synth
 
 pytestmark = pytest.mark.gpu
@@ -55,6 +63,32 @@ def test_sampled_plane_vs_oracle(big, k):
     ref = oracle.integral_histogram_plane(img, NBINS, k)
     got = out[k].cpu().numpy().view(np.uint32)
     assert np.array_equal(got, ref), "plane %d: %d words differ" % (k, int((got != ref).sum()))
+
+
+def test_every_plane_vs_oracle_by_digest(big):
+    # all 128 planes (32 GiB): the oracle computes every plane in spawned
+    # host processes while the GPU planes are copied back and hashed in
+    # threads; equal SHA-256 digests per plane mean equal words.  A worker
+    # that dies breaks the pool with an error (no silent wait).
+    img, _, _, out, _, _, _ = big
+    oracle.default()  # the oracle library exists before any worker loads it
+    nproc = max(1, min(16, os.cpu_count() or 1))
+    with cf.ProcessPoolExecutor(nproc, mp_context=multiprocessing.get_context("spawn"),
+                                initializer=oracle_planes.init, initargs=(img,)) as pool:
+        pending = [pool.submit(oracle_planes.plane_digest, (NBINS, k)) for k in range(NBINS)]
+
+        def gpu_digest(k):
+            return k, hashlib.sha256(out[k].cpu().numpy()).hexdigest()
+
+        with cf.ThreadPoolExecutor(8) as ex:
+            got = dict(ex.map(gpu_digest, range(NBINS)))
+        ref = dict(f.result(timeout=1200) for f in pending)
+    bad = [k for k in range(NBINS) if got[k] != ref[k]]
+    if bad:
+        k = bad[0]
+        plane = out[k].cpu().numpy().view(np.uint32)
+        want = oracle.integral_histogram_plane(img, NBINS, k)
+        raise AssertionError("%d planes differ; plane %d: %d words" % (len(bad), k, int((plane != want).sum())))
 
 
 def test_every_word_by_second_difference(big):
