@@ -305,7 +305,9 @@ def configs_report(stream, peak: float) -> dict:
     rects = torch.from_numpy(synth.rects(seed + 1, 1000, h, w)).cuda()
     q = torch.empty((1000, b), dtype=torch.int32, device="cuda")
     byts = 64 * (h * w * b * 4 + h * w)
-    for label, tune in (("vga_640x480_b32_1000q", None), ("vga_640x480_b32_1000q_overlapped", {"overlap": 1})):
+    vga_tuned = autotune.tune_plan(h, w, b)
+    for label, tune in (("vga_640x480_b32_1000q", None), ("vga_640x480_b32_1000q_overlapped", {"overlap": 1}),
+                        ("vga_640x480_b32_1000q_autotuned", dict(vga_tuned, overlap=1))):
         with ihist.Plan(h, w, b, tune=tune) as plan:
             def vga():
                 for i in range(64):
@@ -316,7 +318,8 @@ def configs_report(stream, peak: float) -> dict:
                 raise SystemExit("device status error in the 640x480 run")
             rep[label] = {"frames_per_s": 64e3 / ms, "us_per_frame": ms * 1e3 / 64,
                           "gbs": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak,
-                          "form": "ihist_compute + ihist_query per frame" + (", overlap=1" if tune else "")}
+                          "form": "ihist_compute + ihist_query per frame" + (", overlap=1" if tune else ""),
+                          "tile": plan.tune}
     del fr, ou, rects, q
     # 256 uneven frames in one launch
     specs = synth.uneven_batch_specs(synth.workload_seed(3), 256)
@@ -648,7 +651,8 @@ def main():
 
     # ---- end-to-end: pinned host frames -> copy stream -> batched compute ->
     # batched query -> host; two 32-frame batches alternate so one batch's
-    # upload overlaps the other's compute ----
+    # upload overlaps the other's compute, and the step's query rows go back
+    # on a third stream under the next step's first compute ----
     e2e_steps = args.e2e_steps or min(args.steps, 30)
     half = NFRAMES // 2
     h_frames = torch.from_numpy(frames).pin_memory()
@@ -657,6 +661,9 @@ def main():
     halves = [ihist.Batch([d_in2[f] for f in range(g * half, (g + 1) * half)], NBINS, [layout] * half,
                           outs=[outs[f] for f in range(g * half, (g + 1) * half)]) for g in range(2)]
     copy_stream = torch.cuda.Stream(dev)
+    d2h_stream = torch.cuda.Stream(dev)
+    ev_queried, ev_copied = torch.cuda.Event(), torch.cuda.Event()
+    ev_copied.record(d2h_stream)
     hq = [h_frames[f] for f in range(NFRAMES)]
     qsz = half * NRECTS * NBINS
 
@@ -664,9 +671,15 @@ def main():
         for g in range(2):
             ihist.ihist_batch_upload_compute(halves[g].handle, [x.data_ptr() for x in hq[g * half:(g + 1) * half]],
                                              s, copy_stream.cuda_stream)
+            if g == 0:
+                stream.wait_event(ev_copied)  # the previous step's rows have left d_query
             ihist.ihist_batch_query_all(halves[g].handle, d_rects[g * half:].data_ptr(), NRECTS,
                                         d_query[g * qsz:].data_ptr(), s)
-        h_query.copy_(d_query, non_blocking=True)
+        ev_queried.record(stream)
+        d2h_stream.wait_event(ev_queried)
+        with torch.cuda.stream(d2h_stream):
+            h_query.copy_(d_query, non_blocking=True)
+        ev_copied.record(d2h_stream)
 
     for _ in range(2):
         e2e_step()
@@ -679,6 +692,7 @@ def main():
     copy_stream.wait_event(e_start)
     for _ in range(e2e_steps):
         e2e_step()
+    stream.wait_event(ev_copied)  # the last step's result is on the host
     e_end.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e_start.elapsed_time(e_end)
@@ -748,7 +762,8 @@ def main():
                     "steps": e2e_steps,
                     "api": "ihist_batch_upload_compute on two alternating %d-frame batches (pinned host frames, "
                            % (NFRAMES // 2) +
-                           "copy stream) + ihist_batch_query_all + copy of the query results to pinned host"},
+                           "copy stream) + ihist_batch_query_all + copy of the query results to pinned host "
+                           "(on a third stream, under the next step's first compute)"},
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
         }
