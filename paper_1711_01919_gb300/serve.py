@@ -101,6 +101,16 @@ def hist_bytes(h: int, w: int, nbins: int) -> int:
     return h * w * nbins * 4
 
 
+# Widest frame a batched launch takes (16-warp CTAs, 4 chunks of 128 columns each).
+MAX_BATCH_WIDTH = 8192
+
+
+def frame_supported(h: int, w: int, nbins: int) -> bool:
+    """Shapes both executors take: the library's frame limits (1 <= h, w <=
+    65535, h * w < 2^32, 1 <= nbins <= 256) and the batched launch's width."""
+    return 1 <= h <= 65535 and 1 <= w <= MAX_BATCH_WIDTH and h * w < (1 << 32) and 1 <= nbins <= 256
+
+
 class HistStore:
     """Resident histograms under a byte budget; LRU over entries not pinned."""
 
@@ -264,7 +274,7 @@ class Server:
             while admit_frames:
                 r = admit_frames[0]
                 nb = hist_bytes(r.h, r.w, r.nbins)
-                if nb > self.store.budget:
+                if nb > self.store.budget or not frame_supported(r.h, r.w, r.nbins):
                     admit_frames.popleft()
                     self.done.append(Done(r.rid, "frame", r.t_arrival, t, "rejected"))
                     continue
