@@ -174,6 +174,34 @@ static void default_tiling(int h, int ngroups, int wpg, int G, int nchunks, int 
       }
     }
   }
+  // A frame that fills less than one wave even in the smallest bands (the
+  // score above then settles on the smallest R) runs each CTA's one item at
+  // a time: its time grows with the band's rows and with the look-back
+  // chain (the band count).  Measured on 640x480 x 32, T ~ 0.18 R + 0.085
+  // (h / R) us (R = 8: 25.3 us, 16: 24.2, 24: 24.8), so R near sqrt(h / 2)
+  // instead (640x480 x 32: 29.1 -> 24.8 us per frame; 1280x720 x 16: 34.5 ->
+  // 30.9 us).  Frames for which the score picked a larger R keep it: there
+  // the larger sqrt(h / 2) measured slower (1280x720 x 32, 1920x1080 x 16).
+  if (!*R && best_r == std::min(h, 8)) {
+    const int NW = best_g * wpg;
+    const int ngsets = (ngroups + best_g - 1) / best_g;
+    const size_t smem0 = smem_layout(NW, best_r, G, nchunks * best_g, pm_staged(layout, G)).bytes;
+    const long long slots0 = (long long)occupancy(fn, NW * 32, smem0) * sms;
+    if ((long long)((h + best_r - 1) / best_r) * ngsets <= slots0) {
+      double best_t = 1e30;
+      int pick = best_r;
+      for (int r = std::min(h, 8); r <= std::min(h, 255); ++r) {
+        const size_t smem = smem_layout(NW, r, G, nchunks * best_g, pm_staged(layout, G)).bytes;
+        if (smem > optin || occupancy(fn, NW * 32, smem) < 1) break;
+        const double t = r + 0.5 * ((h + r - 1) / r);
+        if (t < best_t) {
+          best_t = t;
+          pick = r;
+        }
+      }
+      best_r = pick;
+    }
+  }
   *R = best_r;
   *gpc = best_g;
 }
