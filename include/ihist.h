@@ -325,8 +325,9 @@ typedef struct {
  * pixel-major; 16 gives IHIST_ERR_UNSUPPORTED) and later bindings may mix
  * table and uniform frames; a batch planned without tables refuses tables
  * later (IHIST_ERR_UNSUPPORTED).  A table entry outside [-1, nbins) gives
- * IHIST_ERR_INVALID_ARG.  Allocates the batch's device workspace and pinned
- * staging buffers. */
+ * IHIST_ERR_INVALID_ARG.  A launch works through the bound frames largest
+ * output first (results do not depend on the order).  Allocates the batch's
+ * device workspace and pinned staging buffers. */
 int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_tune_t *tune,
                      ihist_batch_t *out);
 

