@@ -55,8 +55,8 @@ def parse_args():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (640x480, uneven 256-frame batch, 8192x8192) "
                          "and the other bin structures (edges, joint RGB)")
-    ap.add_argument("--layout", choices=("bin", "pixel"), default="bin",
-                    help="output layout of the timed path (the workload's is bin-major; pixel for captures)")
+    ap.add_argument("--layout", choices=("bin", "pixel", "quad"), default="bin",
+                    help="output layout of the timed path (the workload's is bin-major; the others for captures)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="simulated seconds of the serving workload per server mode (0 = skip)")
     ap.add_argument("--frames", type=int, default=64,
@@ -331,7 +331,7 @@ def configs_report(stream, peak: float) -> dict:
     # the autotuner picks the layout (no queries in this workload) and, for
     # it, the launch shape
     auto_layout, auto_tune, layout_ms = autotune.tune_batch_layout([(h, w, nb) for (h, w, nb, sd) in specs], 0)
-    names = {ihist.IHIST_BIN_MAJOR: "bin-major", ihist.IHIST_PIXEL_MAJOR: "pixel-major"}
+    names = {ihist.IHIST_BIN_MAJOR: "bin-major", ihist.IHIST_PIXEL_MAJOR: "pixel-major", ihist.IHIST_QUAD_MAJOR: "quad-major"}
     for label, tune, layout in (("default", None, ihist.IHIST_BIN_MAJOR), ("autotuned", auto_tune, auto_layout)):
         with ihist.Batch(fr, nbs, [layout] * len(fr), outs=ou, tune=tune or None) as batch:
             ms = _median_ms(batch.compute, stream)
@@ -466,6 +466,48 @@ def host_output_report(stream, peak: float, n: int = 16) -> dict:
             "form": "ihist_compute with d_out in page-locked host memory (bin-major)"}
 
 
+def layouts_report(d_frames, outs, d_rects, stream, steps: int = 10) -> dict:
+    """The bench step (one batched launch over the resident frames + one
+    batched query launch) in each output layout, on the same frames and the
+    same output memory."""
+    import torch
+
+    from paper_1711_01919_gb300 import ihist
+    n = d_frames.shape[0]
+    s = stream.cuda_stream
+    flat = outs.view(-1)
+    out = {}
+    byts = n * (H * W * NBINS * 4 + H * W)
+    for name, layout in (("bin-major", ihist.IHIST_BIN_MAJOR), ("pixel-major", ihist.IHIST_PIXEL_MAJOR),
+                         ("quad-major", ihist.IHIST_QUAD_MAJOR)):
+        o = flat.view((n,) + ihist.out_shape(H, W, NBINS, layout))
+        q = torch.empty((n * NRECTS * NBINS,), dtype=torch.int32, device=flat.device)
+        with ihist.Batch([d_frames[f] for f in range(n)], NBINS, [layout] * n, outs=[o[f] for f in range(n)]) as b:
+            def step():
+                ihist.ihist_batch_compute(b.handle, s)
+                ihist.ihist_batch_query_all(b.handle, d_rects.data_ptr(), NRECTS, q.data_ptr(), s)
+
+            for _ in range(3):
+                step()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for _ in range(steps):
+                ihist.ihist_batch_compute(b.handle, s)
+            ev[1].record(stream)
+            for _ in range(steps):
+                ihist.ihist_batch_query_all(b.handle, d_rects.data_ptr(), NRECTS, q.data_ptr(), s)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            if b.status() != ihist.IHIST_OK:
+                raise SystemExit("device status error in the %s run" % name)
+            scan_ms, query_ms = ev[0].elapsed_time(ev[1]) / steps, ev[1].elapsed_time(ev[2]) / steps
+            out[name] = {"scan_ms": scan_ms, "query_ms": query_ms,
+                         "frames_per_s": n * 1e3 / (scan_ms + query_ms), "scan_gbs": byts / scan_ms / 1e6}
+        del q
+    return out
+
+
 def other_bins_report(d_frames, outs, stream, steps: int = 5) -> dict:
     """Per-frame launches with other bin structures on the same 1080p
     frames and output buffers: 64 non-uniform bins given by edges, and the
@@ -565,7 +607,8 @@ def main():
     d_frames = torch.from_numpy(frames).to(dev)
     # every frame queries the same rectangles: [frames][rects][4]
     d_rects = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(rects, (NFRAMES,) + rects.shape))).to(dev)
-    layout = ihist.IHIST_PIXEL_MAJOR if args.layout == "pixel" else ihist.IHIST_BIN_MAJOR
+    layout = {"bin": ihist.IHIST_BIN_MAJOR, "pixel": ihist.IHIST_PIXEL_MAJOR,
+              "quad": ihist.IHIST_QUAD_MAJOR}[args.layout]
     outs = torch.empty((NFRAMES,) + ihist.out_shape(H, W, NBINS, layout), dtype=torch.int32, device=dev)
     d_query = torch.empty((NFRAMES * NRECTS * NBINS,), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -703,6 +746,7 @@ def main():
         raise SystemExit("e2e query results differ from the device-resident run")
 
     other_bins = None if args.no_configs else other_bins_report(d_frames, outs, stream)
+    layouts = None if args.no_configs else layouts_report(d_frames, outs, d_rects, stream)
 
     # ---- write-only probe: the store bandwidth a plain fill reaches on this GPU ----
     probe = torch.empty((1 << 30,), dtype=torch.int32, device=dev)
@@ -732,7 +776,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {
                 "workload": WORKLOAD, "frames_per_step": NFRAMES, "H": H, "W": W, "B": NBINS,
-                "layout": "bin-major" if layout == ihist.IHIST_BIN_MAJOR else "pixel-major",
+                "layout": {ihist.IHIST_BIN_MAJOR: "bin-major", ihist.IHIST_PIXEL_MAJOR: "pixel-major",
+                           ihist.IHIST_QUAD_MAJOR: "quad-major"}[layout],
                 "queries_per_frame": NRECTS,
                 "form": "batched: one persistent scan launch over the %d resident frames + one query launch" % NFRAMES,
                 "parallelism": "replicas (one independent 64-frame sequence per GPU)" if world > 1 else "single GPU",
@@ -771,6 +816,9 @@ def main():
             for v in other_bins.values():
                 v["frac"] = v["gbs"] / peak
             line["other_bins"] = other_bins
+            for v in layouts.values():
+                v["scan_frac"] = v["scan_gbs"] / peak
+            line["layouts_64x1080p_b64_1000q"] = layouts
             line["other_workloads"] = configs_report(stream, peak)
         if args.serve_seconds > 0:
             line["serving"] = serving_report(args.serve_seconds)

@@ -8,8 +8,9 @@ timed with CUDA events on a seeded uniform frame (median of a few launches
 after warm-up); candidates the library rejects (shared memory, registers)
 are skipped.  For a batch the search covers R and G of the batched launch.
 ``choose_layout`` (one frame) and ``tune_batch_layout`` (a batch) time
-compute plus a query load for bin-major and pixel-major output and keep the
-faster, for callers that accept either.
+compute plus a query load for bin-major, pixel-major and (bin counts that
+are multiples of 4) quad-major output and keep the fastest, for callers
+that accept any.
 
 Results are cached in a JSON file (``IHIST_TUNE_CACHE`` or
 ``~/.cache/ihist_tune.json``) keyed by device name and shape.  The timing
@@ -194,6 +195,15 @@ def tune_batch(shapes, timer=None, device=None, use_cache=True, tables=False):
     return best
 
 
+def layouts_for(nbins_list):
+    """Layouts every frame can take: bin-major, pixel-major, and quad-major
+    when every bin count is a multiple of 4."""
+    out = [ihist.IHIST_BIN_MAJOR, ihist.IHIST_PIXEL_MAJOR]
+    if all(b % 4 == 0 for b in nbins_list):
+        out.append(ihist.IHIST_QUAD_MAJOR)
+    return out
+
+
 def tune_batch_layout(shapes, queries_per_frame=0, timer=None, device=None, use_cache=True):
     """Layout and launch shape of a batch of (h, w, nbins) frames that are
     computed once and then queried `queries_per_frame` times each.  For each
@@ -203,7 +213,7 @@ def tune_batch_layout(shapes, queries_per_frame=0, timer=None, device=None, use_
     measurement (tests).  Returns (layout, tune, {layout: ms})."""
     device = device or _device_key()
     times, tunes = {}, {}
-    for layout in (ihist.IHIST_BIN_MAJOR, ihist.IHIST_PIXEL_MAJOR):
+    for layout in layouts_for([b for (h, w, b) in shapes]):
         sh = [(h, w, b, layout) for (h, w, b) in shapes]
         shape_timer = None if timer is None else (lambda t, sh=sh: timer(sh, t, 0))
         try:
@@ -219,8 +229,9 @@ def tune_batch_layout(shapes, queries_per_frame=0, timer=None, device=None, use_
 
 
 def choose_layout(h, w, nbins, queries_per_frame=1000, timer=None):
-    """Bin-major or pixel-major for a frame that is computed once and then
-    queried `queries_per_frame` times: whichever takes less time in total."""
+    """The layout (bin-major, pixel-major or, when nbins % 4 == 0,
+    quad-major) for a frame that is computed once and then queried
+    `queries_per_frame` times: whichever takes less time in total."""
     if timer is None:
         import torch
 
@@ -242,6 +253,5 @@ def choose_layout(h, w, nbins, queries_per_frame=1000, timer=None):
                 b.record()
                 torch.cuda.synchronize()
                 return a.elapsed_time(b) / 3
-    t_bm = timer(ihist.IHIST_BIN_MAJOR)
-    t_pm = timer(ihist.IHIST_PIXEL_MAJOR)
-    return ihist.IHIST_PIXEL_MAJOR if t_pm < t_bm else ihist.IHIST_BIN_MAJOR
+    times = {layout: timer(layout) for layout in layouts_for([nbins])}
+    return min(times, key=times.get)

@@ -96,7 +96,9 @@ int ihist::host::validate_shape(int h, int w, int nbins, int layout) {
   if (h < 1 || w < 1 || h > 65535 || w > 65535) return IHIST_ERR_INVALID_ARG;
   if ((unsigned long long)h * (unsigned long long)w >= (1ull << 32)) return IHIST_ERR_INVALID_ARG;
   if (nbins < 1 || nbins > 256) return IHIST_ERR_INVALID_ARG;
-  if (layout != IHIST_BIN_MAJOR && layout != IHIST_PIXEL_MAJOR) return IHIST_ERR_INVALID_ARG;
+  if (layout != IHIST_BIN_MAJOR && layout != IHIST_PIXEL_MAJOR && layout != IHIST_QUAD_MAJOR)
+    return IHIST_ERR_INVALID_ARG;
+  if (layout == IHIST_QUAD_MAJOR && nbins % 4 != 0) return IHIST_ERR_INVALID_ARG;
   if (w > 16384) return IHIST_ERR_UNSUPPORTED;
   return IHIST_OK;
 }
@@ -603,7 +605,9 @@ int ihist::host::launch_query(int H, int W, int B, int layout, int sms, Ctrl *ct
   const cudaError_t e =
       layout == IHIST_BIN_MAJOR
           ? cudaLaunchKernelEx(&cfg, query_kernel<0>, d_hist, H, W, B, d_rects, total, d_hist_out, ctrl)
-          : cudaLaunchKernelEx(&cfg, query_kernel<1>, d_hist, H, W, B, d_rects, total, d_hist_out, ctrl);
+      : layout == IHIST_PIXEL_MAJOR
+          ? cudaLaunchKernelEx(&cfg, query_kernel<1>, d_hist, H, W, B, d_rects, total, d_hist_out, ctrl)
+          : cudaLaunchKernelEx(&cfg, query_kernel<2>, d_hist, H, W, B, d_rects, total, d_hist_out, ctrl);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return IHIST_ERR_CUDA;
@@ -629,6 +633,7 @@ extern "C" int ihist_window_search(ihist_plan_t p, const uint32_t *d_hist, const
   if (((uintptr_t)d_hist & 3u) || ((uintptr_t)d_target & 3u) || ((uintptr_t)d_scores & 3u) ||
       ((uintptr_t)d_best & 7u))
     return IHIST_ERR_INVALID_ARG;
+  if (p->layout == IHIST_QUAD_MAJOR) return IHIST_ERR_UNSUPPORTED;
   int rc = check_device(p);
   if (rc != IHIST_OK) return rc;
   if (d_best && cudaMemsetAsync(d_best, 0, sizeof(unsigned long long), (cudaStream_t)stream) != cudaSuccess)

@@ -81,6 +81,13 @@ __device__ __forceinline__ void st_stream_v4(uint32_t *p, uint32_t a, uint32_t b
                : "memory");
 }
 
+// Streaming 256-bit store (32-byte aligned p): one full DRAM sector.
+__device__ __forceinline__ void st_stream_v8(uint32_t *p, uint4 a, uint4 b) {
+  asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a.x), "r"(a.y),
+               "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+               : "memory");
+}
+
 __device__ __forceinline__ void st_stream(uint32_t *p, uint32_t a) {
   asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(a) : "memory");
 }

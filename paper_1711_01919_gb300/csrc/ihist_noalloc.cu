@@ -118,7 +118,9 @@ extern "C" int ihist_compute_noalloc(int h, int w, int nbins, int layout, const 
                                      int *device_status) {
   if (h < 1 || w < 1 || h > 65535 || w > 65535 || nbins < 1 || nbins > 256) return IHIST_ERR_INVALID_ARG;
   if ((unsigned long long)h * (unsigned long long)w >= (1ull << 32)) return IHIST_ERR_INVALID_ARG;
-  if (layout != IHIST_BIN_MAJOR && layout != IHIST_PIXEL_MAJOR) return IHIST_ERR_INVALID_ARG;
+  if (layout != IHIST_BIN_MAJOR && layout != IHIST_PIXEL_MAJOR && layout != IHIST_QUAD_MAJOR)
+    return IHIST_ERR_INVALID_ARG;
+  if (layout == IHIST_QUAD_MAJOR && nbins % 4 != 0) return IHIST_ERR_INVALID_ARG;
   if (!d_in || !d_out || in_pitch < (size_t)w || in_pitch > (size_t)LLONG_MAX) return IHIST_ERR_INVALID_ARG;
   if (((uintptr_t)d_out & 3u) != 0) return IHIST_ERR_INVALID_ARG;
   int dev = 0;

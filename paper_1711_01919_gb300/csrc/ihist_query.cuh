@@ -12,7 +12,9 @@ namespace ihist {
 
 // One thread per (rectangle, bin) pair p = r * B + b, grid-stride.  Output
 // row r of [n][B] is written by B consecutive threads (coalesced).  The
-// rectangle's four ints are re-read by its B threads and served by L1.
+// rectangle's four ints are re-read by its B threads and served by L1.  In
+// the quad-major layout the four threads of a quad read one 16-byte word per
+// corner (one DRAM sector for four bins).
 template <int LAYOUT>
 __global__ void __launch_bounds__(256) query_kernel(const uint32_t *__restrict__ hist, int H,
                                                      int W, int B,
@@ -34,8 +36,9 @@ __global__ void __launch_bounds__(256) query_kernel(const uint32_t *__restrict__
     if (ok) {
       // element offset of H at (row y, column x) for this bin
       auto at = [&](int y, int x) -> size_t {
-        return LAYOUT == 0 ? (size_t)b * plane + (size_t)y * W + x
-                           : ((size_t)y * W + x) * (size_t)B + b;
+        return LAYOUT == 0   ? (size_t)b * plane + (size_t)y * W + x
+               : LAYOUT == 1 ? ((size_t)y * W + x) * (size_t)B + b
+                             : ((size_t)(b >> 2) * plane + (size_t)y * W + x) * 4 + (b & 3);
       };
       v = __ldg(hist + at(y1, x1));
       if (y0 > 0) v -= __ldg(hist + at(y0 - 1, x1));
@@ -89,9 +92,10 @@ __global__ void __launch_bounds__(256) query_batch_kernel(const Desc *frames,
     uint32_t v = 0u;
     if (ok) {
       const size_t plane = (size_t)H * (size_t)W;
-      const bool bm = (layout == 0);
       auto at = [&](int y, int x) -> size_t {
-        return bm ? (size_t)b * plane + (size_t)y * W + x : ((size_t)y * W + x) * (size_t)B + b;
+        return layout == 0   ? (size_t)b * plane + (size_t)y * W + x
+               : layout == 1 ? ((size_t)y * W + x) * (size_t)B + b
+                             : ((size_t)(b >> 2) * plane + (size_t)y * W + x) * 4 + (b & 3);
       };
       v = __ldg(hist + at(y1, x1));
       if (y0 > 0) v -= __ldg(hist + at(y0 - 1, x1));

@@ -30,6 +30,7 @@ IHIST_ERR_BAD_RECT = 6
 IHIST_ERR_CHECK_FAILED = 7
 IHIST_BIN_MAJOR = 0
 IHIST_PIXEL_MAJOR = 1
+IHIST_QUAD_MAJOR = 2  # H[b/4][y][x][b%4]
 
 EXPORTED = (
     "ihist_plan", "ihist_plan_tuned", "ihist_plan_get_tune", "ihist_workspace_bytes",
@@ -464,9 +465,7 @@ class Plan:
 
     @property
     def out_shape(self):
-        if self.layout == IHIST_BIN_MAJOR:
-            return (self.nbins, self.h, self.w)
-        return (self.h, self.w, self.nbins)
+        return out_shape(self.h, self.w, self.nbins, self.layout)
 
     def empty_output(self, device=None):
         import torch
@@ -557,7 +556,12 @@ class Plan:
 
 
 def out_shape(h: int, w: int, nbins: int, layout: int):
-    return (nbins, h, w) if layout == IHIST_BIN_MAJOR else (h, w, nbins)
+    """Shape of H in a layout: [B][h][w], [h][w][B] or [B/4][h][w][4]."""
+    if layout == IHIST_BIN_MAJOR:
+        return (nbins, h, w)
+    if layout == IHIST_QUAD_MAJOR:
+        return (nbins // 4, h, w, 4)
+    return (h, w, nbins)
 
 
 class Batch:

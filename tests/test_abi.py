@@ -44,7 +44,7 @@ def test_output_bytes_and_error_strings(lib):
 
 
 @pytest.mark.parametrize("h,w,b,layout", [(0, 10, 4, 0), (10, 0, 4, 0), (65536, 4, 4, 0), (4, 4, 0, 0),
-                                          (4, 4, 257, 0), (4, 4, 4, 2), (70000, 70000, 4, 0)])
+                                          (4, 4, 257, 0), (4, 4, 4, 3), (4, 4, 6, 2), (70000, 70000, 4, 0)])
 def test_plan_rejects_bad_shapes_before_touching_cuda(lib, h, w, b, layout):
     with pytest.raises(ihist.IhistError) as e:
         ihist.ihist_plan(h, w, b, layout)

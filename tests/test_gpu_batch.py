@@ -24,6 +24,9 @@ def u32(t):
 
 def ref_layout(img, nbins, layout):
     ref = oracle.integral_histogram(img, nbins)
+    if layout == ihist.IHIST_QUAD_MAJOR:
+        b, h, w = ref.shape
+        return np.ascontiguousarray(ref.reshape(b // 4, 4, h, w).transpose(0, 2, 3, 1))
     return ref if layout == 0 else np.ascontiguousarray(ref.transpose(1, 2, 0))
 
 
@@ -248,7 +251,7 @@ def test_autotuned_layout_and_launch_shape_give_exact_batches(tmp_path, monkeypa
     nbins = [b for (h, w, b) in shapes]
     for queries in (0, 4000):
         layout, tune, times = autotune.tune_batch_layout(shapes, queries, use_cache=False)
-        assert set(times) == {ihist.IHIST_BIN_MAJOR, ihist.IHIST_PIXEL_MAJOR}
+        assert set(times) == {ihist.IHIST_BIN_MAJOR, ihist.IHIST_PIXEL_MAJOR, ihist.IHIST_QUAD_MAJOR}
         assert times[layout] == min(times.values())
         with ihist.Batch([torch.from_numpy(x).cuda() for x in imgs], nbins, [layout] * 3, tune=tune or None) as batch:
             batch.compute()

@@ -23,11 +23,14 @@ assert ihist.LIB_PATH.endswith("libihist_checked.so"), ihist.LIB_PATH
 def u32(t): return t.cpu().numpy().view(np.uint32)
 def ref_layout(img, b, l):
     r = oracle.integral_histogram(img, b)
+    if l == 2:
+        return np.ascontiguousarray(r.reshape(b // 4, 4, r.shape[1], r.shape[2]).transpose(0, 2, 3, 1))
     return r if l == 0 else np.ascontiguousarray(r.transpose(1, 2, 0))
 n = 0
 for (h, w, b, l, tune) in [(1, 1, 3, 0, None), (37, 131, 16, 0, None), (64, 257, 7, 1, None), (100, 1000, 64, 1, None),
                            (33, 2049, 100, 0, {"bins_per_cta": 8}), (130, 640, 64, 1, {"bins_per_cta": 8}),
-                           (300, 4096, 8, 0, None), (17, 128, 256, 1, None)]:
+                           (300, 4096, 8, 0, None), (17, 128, 256, 1, None), (37, 131, 16, 2, None),
+                           (130, 643, 64, 2, {"bins_per_cta": 16})]:
     img = synth.uniform_frame(h + w + b, h, w)
     with ihist.Plan(h, w, b, l, tune=tune) as p:
         got = u32(p.compute(torch.from_numpy(img).cuda())).reshape(p.out_shape)
@@ -44,7 +47,7 @@ with ihist.Plan(60, 300, bins_per_channel=[4, 4, 4]) as p:
     got = u32(p.compute(torch.from_numpy(rgb).cuda()))
     assert p.status() == ihist.IHIST_OK
 assert np.array_equal(got.reshape(64, 60, 300), oracle.integral_histogram_joint(rgb, [4, 4, 4]))
-shapes = [(37, 131, 16, 0), (240, 320, 16, 1), (100, 1000, 64, 0), (720, 1280, 32, 1), (5, 3, 3, 1)]
+shapes = [(37, 131, 16, 0), (240, 320, 16, 1), (100, 1000, 64, 0), (720, 1280, 32, 1), (5, 3, 3, 1), (90, 250, 12, 2)]
 imgs = [synth.uniform_frame(40 + i, h, w) for i, (h, w, b, l) in enumerate(shapes)]
 with ihist.Batch([torch.from_numpy(x).cuda() for x in imgs], [s[2] for s in shapes], [s[3] for s in shapes]) as bt:
     bt.compute()

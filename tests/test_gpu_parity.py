@@ -31,6 +31,9 @@ def u32(t):
 
 def to_layout(ref, layout):
     """Bin-major oracle result in the requested layout (a transpose only)."""
+    if layout == ihist.IHIST_QUAD_MAJOR:
+        b, h, w = ref.shape
+        return np.ascontiguousarray(ref.reshape(b // 4, 4, h, w).transpose(0, 2, 3, 1))
     return ref if layout == ihist.IHIST_BIN_MAJOR else np.ascontiguousarray(ref.transpose(1, 2, 0))
 
 
