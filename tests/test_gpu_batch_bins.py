@@ -37,6 +37,9 @@ def reference(img, nbins, table, layout):
         ref = oracle.integral_histogram(img, nbins)
     else:
         ref = oracle.integral_histogram_mapped(img, np.asarray(table, dtype=np.int32), nbins)
+    if layout == 2:
+        b, h, w = ref.shape
+        return np.ascontiguousarray(ref.reshape(b // 4, 4, h, w).transpose(0, 2, 3, 1))
     return ref if layout == 0 else np.ascontiguousarray(ref.transpose(1, 2, 0))
 
 
@@ -49,7 +52,8 @@ def check(batch, imgs, nbins, tables, layouts):
 
 
 CASES = [(1, 1, 3, 0), (37, 131, 16, 0), (240, 320, 16, 1), (480, 640, 32, 0), (64, 257, 7, 1),
-         (720, 1280, 64, 0), (33, 2049, 100, 0), (17, 128, 256, 1), (200, 700, 5, 0)]
+         (720, 1280, 64, 0), (33, 2049, 100, 0), (17, 128, 256, 1), (200, 700, 5, 0), (90, 333, 12, 2),
+         (240, 320, 64, 2)]
 
 
 def frames_and_tables(seed, cases):
@@ -162,7 +166,7 @@ def joint_frame(seed, h, w, c):
 
 JOINT_CASES = [  # (h, w, bins per channel, layout)
     (150, 300, [4, 4, 4], 0), (64, 257, [8, 2], 1), (37, 131, [2, 2, 2, 2], 0), (240, 320, [16, 16], 0),
-    (1, 5, [3, 5], 1), (200, 700, [5], None)]
+    (1, 5, [3, 5], 1), (200, 700, [5], None), (120, 250, [4, 2, 2], 2)]
 
 
 @pytest.mark.parametrize("with_tables", [False, True])
@@ -179,7 +183,10 @@ def test_joint_frames_next_to_uniform_and_table_frames(with_tables):
         nb = int(np.prod(bins))
         frames.append(img), nbins.append(nb), layouts.append(l), tables.append(None), joint.append(bins)
         ref = oracle.integral_histogram_joint(img, bins)
-        refs.append(ref if l == 0 else np.ascontiguousarray(ref.transpose(1, 2, 0)))
+        if l == 2:
+            refs.append(np.ascontiguousarray(ref.reshape(nb // 4, 4, h, w).transpose(0, 2, 3, 1)))
+        else:
+            refs.append(ref if l == 0 else np.ascontiguousarray(ref.transpose(1, 2, 0)))
     with ihist.Batch([torch.from_numpy(x).cuda() for x in frames], nbins, layouts, tables=tables,
                      joint=joint) as batch:
         for _ in range(2):  # the joint-bin planes are recomputed each launch

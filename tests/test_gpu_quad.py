@@ -134,3 +134,16 @@ def test_host_memory_output():
         torch.cuda.synchronize()
         assert plan.status() == ihist.IHIST_OK
         assert_same(host.numpy().view(np.uint32), quad(oracle.integral_histogram(img, nbins)), "host output")
+
+
+def test_other_bin_structures_in_quad_major():
+    h, w = 150, 300
+    edges = [0, 10, 50, 51, 200, 210, 220, 240, 256]  # 8 bins
+    img = synth.gradient_frame(1500, h, w)
+    rgb = np.ascontiguousarray(np.stack([synth.uniform_frame(1501 + c, h, w) for c in range(3)], axis=2))
+    with ihist.Plan(h, w, layout=Q, edges=edges) as ep, ihist.Plan(h, w, layout=Q, bins_per_channel=[4, 2, 2]) as jp:
+        he = ep.compute(torch.from_numpy(img).cuda())
+        hj = jp.compute(torch.from_numpy(rgb).cuda())
+        assert ep.status() == ihist.IHIST_OK and jp.status() == ihist.IHIST_OK
+        assert_same(u32(he).reshape(ep.out_shape), quad(oracle.integral_histogram_edges(img, edges)), "edges")
+        assert_same(u32(hj).reshape(jp.out_shape), quad(oracle.integral_histogram_joint(rgb, [4, 2, 2])), "joint")
