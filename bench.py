@@ -745,6 +745,37 @@ def main():
     if not torch.equal(h_query.view(NFRAMES, NRECTS, NBINS)[NFRAMES - 1], resident_query):
         raise SystemExit("e2e query results differ from the device-resident run")
 
+    # ---- the per-frame form of the same pipeline (Algorithm 6): host frames
+    # through a 2-slot device ring on the copy stream, one overlapped scan and
+    # one query per frame, the query rows back to pinned host memory ----
+    seq_plan = ihist.Plan(H, W, NBINS, layout)
+    slots = torch.empty((2, H, W), dtype=torch.uint8, device=dev)
+    d_q1 = torch.empty((NRECTS * NBINS,), dtype=torch.int32, device=dev)
+    seq_steps = max(3, min(args.steps, 10))
+
+    def seq_step():
+        ihist.ihist_sequence_host(seq_plan.handle, h_frames.data_ptr(), H * W, NFRAMES, slots.data_ptr(),
+                                  outs.data_ptr(), NFRAMES, d_rects.data_ptr(), NRECTS, d_q1.data_ptr(),
+                                  h_query.data_ptr(), s, copy_stream.cuda_stream)
+
+    for _ in range(2):
+        seq_step()
+    torch.cuda.synchronize()
+    q_start, q_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q_start.record(stream)
+    copy_stream.wait_event(q_start)
+    for _ in range(seq_steps):
+        seq_step()
+    q_end.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = q_start.elapsed_time(q_end)
+    if seq_plan.status() != ihist.IHIST_OK:
+        raise SystemExit("device status error in the per-frame sequence")
+    if not torch.equal(h_query.view(NFRAMES, NRECTS, NBINS)[NFRAMES - 1], resident_query):
+        raise SystemExit("per-frame sequence query results differ from the batched run")
+    seq_plan.close()
+    del slots, d_q1
+
     other_bins = None if args.no_configs else other_bins_report(d_frames, outs, stream)
     layouts = None if args.no_configs else layouts_report(d_frames, outs, d_rects, stream)
 
@@ -762,7 +793,8 @@ def main():
     write_probe_gbs = 10 * probe.numel() * 4 / (w_start.elapsed_time(w_end) / 1000.0) / 1e9
     del probe
 
-    elapsed_ms, e2e_ms, plain_ms, overlap_ms = max_over_ranks([elapsed_ms, e2e_ms, plain_ms, overlap_ms], world, dev)
+    elapsed_ms, e2e_ms, plain_ms, overlap_ms, seq_ms = max_over_ranks(
+        [elapsed_ms, e2e_ms, plain_ms, overlap_ms, seq_ms], world, dev)
 
     if rank == 0:
         value = job_throughput(NFRAMES, args.steps, world, elapsed_ms)
@@ -808,7 +840,13 @@ def main():
                     "api": "ihist_batch_upload_compute on two alternating %d-frame batches (pinned host frames, "
                            % (NFRAMES // 2) +
                            "copy stream) + ihist_batch_query_all + copy of the query results to pinned host "
-                           "(on a third stream, under the next step's first compute)"},
+                           "(on a third stream, under the next step's first compute)",
+                    "per_frame_sequence": {
+                        "value": job_throughput(NFRAMES, seq_steps, world, seq_ms), "unit": "frames/s",
+                        "steps": seq_steps,
+                        "api": "ihist_sequence_host: pinned host frames through a 2-slot device ring on the copy "
+                               "stream, one scan (overlapped launch) + one ihist_query per frame, each frame's "
+                               "query rows back to pinned host"}},
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
         }

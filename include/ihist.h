@@ -270,10 +270,13 @@ int ihist_mapping_compute(int mapping, int h, int w, int nbins, const uint8_t *d
  *   d_rects, nrects  optional (nrects may be 0): rectangles queried on every
  *                 frame's histogram (Eq. 2) into d_query (nrects * nbins
  *                 uint32) and copied to h_query_out + i * nrects * nbins.
- * All work is enqueued; the call returns before it finishes.  The caller
- * synchronises `stream` (which the last copy and compute are ordered on)
- * before reading h_query_out or reusing h_frames.  Uses two events the
- * plan owns, so it must not overlap another sequence call on the same plan. */
+ * Frame i+1's upload is issued before frame i's rows go back, and the rows
+ * go back on copy_stream, so the compute stream runs scan, query, scan, ...
+ * (the scans overlapped, see tune.overlap).  All work is enqueued; the call
+ * returns before it finishes.  The caller synchronises `stream` (which is
+ * made to wait for the last copy and compute) before reading h_query_out or
+ * reusing h_frames.  Uses events the plan owns, so it must not overlap
+ * another sequence call on the same plan. */
 int ihist_sequence_host(ihist_plan_t plan, const uint8_t *h_frames, size_t frame_stride,
                         int nframes, uint8_t *d_slots, uint32_t *d_outs, int nouts,
                         const int32_t *d_rects, int nrects, uint32_t *d_query,

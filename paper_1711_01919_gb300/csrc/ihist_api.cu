@@ -64,6 +64,8 @@ struct ihist_plan_s {
   uint32_t *flags, *agg_cnt, *agg_left, *incl;
   cudaEvent_t ev_uploaded[2];  // sequence pipeline: slot filled
   cudaEvent_t ev_consumed[2];  // sequence pipeline: slot read by its compute
+  cudaEvent_t ev_queried;      // sequence pipeline: a frame's query rows are in d_query
+  cudaEvent_t ev_copied;       // sequence pipeline: those rows have reached the host
   struct {
     const void *ptr;
     size_t pitch;
@@ -347,12 +349,15 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   }
   for (int i = 0; i < 2; ++i) {
     if (cudaEventCreateWithFlags(&p->ev_uploaded[i], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_consumed[i], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&p->ev_consumed[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(i == 0 ? &p->ev_queried : &p->ev_copied, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       for (int j = 0; j <= i; ++j) {
         if (p->ev_uploaded[j]) cudaEventDestroy(p->ev_uploaded[j]);
         if (p->ev_consumed[j]) cudaEventDestroy(p->ev_consumed[j]);
       }
+      if (p->ev_queried) cudaEventDestroy(p->ev_queried);
+      if (p->ev_copied) cudaEventDestroy(p->ev_copied);
       cudaFree(p->ws);
       delete p;
       return IHIST_ERR_CUDA;
@@ -682,30 +687,50 @@ extern "C" int ihist_sequence_host(ihist_plan_t p, const uint8_t *h_frames, size
   cudaStream_t s = (cudaStream_t)stream, cs = (cudaStream_t)copy_stream;
   const size_t obytes = ihist_output_bytes(p->H, p->W, p->B);
   const size_t qwords = (size_t)nrects * (size_t)p->B;
+  // frame i's upload into slot i % 2, once the compute that read the slot
+  // (frame i-2) is done
+  auto upload = [&](int i) -> int {
+    const int slot = i & 1;
+    if (i >= 2 && cudaStreamWaitEvent(cs, p->ev_consumed[slot], 0) != cudaSuccess) return IHIST_ERR_CUDA;
+    if (cudaMemcpyAsync(d_slots + (size_t)slot * fbytes, h_frames + (size_t)i * frame_stride, fbytes,
+                        cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaEventRecord(p->ev_uploaded[slot], cs) != cudaSuccess)
+      return IHIST_ERR_CUDA;
+    return IHIST_OK;
+  };
+  rc = upload(0);
+  if (rc != IHIST_OK) return rc;
   for (int i = 0; i < nframes; ++i) {
     const int slot = i & 1;
-    uint8_t *d_in = d_slots + (size_t)slot * fbytes;
-    // the slot may be refilled only once the compute that read it (frame i-2) is done
-    if (i >= 2 && cudaStreamWaitEvent(cs, p->ev_consumed[slot], 0) != cudaSuccess) return IHIST_ERR_CUDA;
-    if (cudaMemcpyAsync(d_in, h_frames + (size_t)i * frame_stride, fbytes, cudaMemcpyHostToDevice,
-                        cs) != cudaSuccess)
-      return IHIST_ERR_CUDA;
-    if (cudaEventRecord(p->ev_uploaded[slot], cs) != cudaSuccess) return IHIST_ERR_CUDA;
+    // frame i+1's upload goes on the copy stream before frame i's copy back,
+    // so it overlaps frame i's compute
+    if (i + 1 < nframes) {
+      rc = upload(i + 1);
+      if (rc != IHIST_OK) return rc;
+    }
     if (cudaStreamWaitEvent(s, p->ev_uploaded[slot], 0) != cudaSuccess) return IHIST_ERR_CUDA;
     uint32_t *d_out = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(d_outs) +
                                                    (size_t)(i % nouts) * obytes);
     // frames arrive by copy, so no kernel before a compute writes its frame
-    rc = compute_frame(p, d_in, row_bytes, d_out, stream, true);
+    rc = compute_frame(p, d_slots + (size_t)slot * fbytes, row_bytes, d_out, stream, true);
     if (rc != IHIST_OK) return rc;
     if (cudaEventRecord(p->ev_consumed[slot], s) != cudaSuccess) return IHIST_ERR_CUDA;
     if (nrects > 0) {
+      // the rows go back on the copy stream, off the compute stream, so the
+      // next frame's scan follows this query directly; d_query is reused
+      // once the previous frame's rows have left it
+      if (i > 0 && cudaStreamWaitEvent(s, p->ev_copied, 0) != cudaSuccess) return IHIST_ERR_CUDA;
       rc = ihist_query(p, d_out, d_rects, nrects, d_query, stream);
       if (rc != IHIST_OK) return rc;
-      if (cudaMemcpyAsync(h_query_out + (size_t)i * qwords, d_query, qwords * sizeof(uint32_t),
-                          cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      if (cudaEventRecord(p->ev_queried, s) != cudaSuccess || cudaStreamWaitEvent(cs, p->ev_queried, 0) != cudaSuccess ||
+          cudaMemcpyAsync(h_query_out + (size_t)i * qwords, d_query, qwords * sizeof(uint32_t),
+                          cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+          cudaEventRecord(p->ev_copied, cs) != cudaSuccess)
         return IHIST_ERR_CUDA;
     }
   }
+  // a caller that synchronises `stream` finds every row on the host
+  if (nrects > 0 && cudaStreamWaitEvent(s, p->ev_copied, 0) != cudaSuccess) return IHIST_ERR_CUDA;
   // later work on the copy stream must not overtake this sequence's computes
   if (cudaStreamWaitEvent(cs, p->ev_consumed[(nframes - 1) & 1], 0) != cudaSuccess) return IHIST_ERR_CUDA;
   return IHIST_OK;
@@ -744,6 +769,8 @@ extern "C" void ihist_destroy(ihist_plan_t p) {
     if (p->ev_uploaded[i]) cudaEventDestroy(p->ev_uploaded[i]);
     if (p->ev_consumed[i]) cudaEventDestroy(p->ev_consumed[i]);
   }
+  if (p->ev_queried) cudaEventDestroy(p->ev_queried);
+  if (p->ev_copied) cudaEventDestroy(p->ev_copied);
   cudaFree(p->ws);
   if (prev != p->device && prev >= 0) cudaSetDevice(prev);
   delete p;

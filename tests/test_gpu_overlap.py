@@ -197,3 +197,31 @@ def test_default_launch_is_safe_when_the_kernel_before_writes_the_frame():
             assert_same(u32(out).reshape(plan.out_shape), ref, "frame xor %#x" % key)
             assert np.array_equal(u32(rows), oracle.query(ref, np.ascontiguousarray(rects[::-1])))
         assert plan.status() == ihist.IHIST_OK
+
+
+def test_sequence_pipeline_rows_and_histograms_after_syncing_the_compute_stream():
+    # 9 host frames through the 2-slot ring, 3 outputs in rotation, 200 rects
+    # per frame; only the compute stream is synchronised before reading
+    h, w, nbins, n, nrects = 180, 300, 16, 9, 200
+    frames = np.stack([synth.uniform_frame(1600 + i, h, w) for i in range(n)])
+    rects = synth.rects(1601, nrects, h, w)
+    hf = torch.from_numpy(frames).pin_memory()
+    slots = torch.empty((2, h, w), dtype=torch.uint8, device="cuda")
+    d_rects = torch.from_numpy(rects).cuda()
+    dq = torch.empty((nrects, nbins), dtype=torch.int32, device="cuda")
+    hq = torch.zeros((n, nrects, nbins), dtype=torch.int32).pin_memory()
+    s, copy = torch.cuda.Stream(), torch.cuda.Stream()
+    with ihist.Plan(h, w, nbins) as plan:
+        outs = torch.empty((3,) + plan.out_shape, dtype=torch.int32, device="cuda")
+        for _ in range(2):  # the plan's events and control blocks are reused by a second call
+            hq.zero_()
+            ihist.ihist_sequence_host(plan.handle, hf.data_ptr(), h * w, n, slots.data_ptr(), outs.data_ptr(), 3,
+                                      d_rects.data_ptr(), nrects, dq.data_ptr(), hq.data_ptr(), s.cuda_stream,
+                                      copy.cuda_stream)
+            s.synchronize()
+            for i in range(n):
+                ref = oracle.integral_histogram(frames[i], nbins)
+                assert np.array_equal(hq[i].numpy().view(np.uint32), oracle.query(ref, rects)), i
+            for i in range(n - 3, n):  # the last frame written to each output
+                assert_same(u32(outs[i % 3]), oracle.integral_histogram(frames[i], nbins), "output of frame %d" % i)
+        assert plan.status() == ihist.IHIST_OK
