@@ -25,7 +25,7 @@ def _lib():
 
 
 @pytest.mark.parametrize("h,w,nbins,layout", [(480, 640, 32, 0), (300, 1000, 24, 1), (1080, 1920, 64, 0),
-                                              (61, 333, 9, 0), (1, 1, 1, 0)])
+                                              (61, 333, 9, 0), (1, 1, 1, 0), (270, 480, 16, 2), (61, 333, 12, 2)])
 def test_noalloc_matches_plan_twice(h, w, nbins, layout):
     s = torch.cuda.current_stream().cuda_stream
     with ihist.Plan(h, w, nbins, layout) as plan:
