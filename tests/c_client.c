@@ -15,6 +15,10 @@
 
 #include "ihist.h"
 
+/* the struct sizes the Python binding mirrors (ctypes) */
+_Static_assert(sizeof(ihist_frame_t) == 72, "ihist_frame_t layout");
+_Static_assert(sizeof(ihist_tune_t) == 40, "ihist_tune_t layout");
+
 static int fail(const char *what, int code) {
   fprintf(stderr, "%s failed: %d (%s)\n", what, code, ihist_error_string(code));
   return 1;
