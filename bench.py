@@ -40,6 +40,7 @@ SIGMA = 20.0
 WORKLOAD = ("sequence of 64 frames 1920x1080 uint8, smooth gradient + Gaussian noise sigma=20 "
             "clipped to [0,255], B=64 uniform bins, uint32 bin-major output, 1000 region queries per frame")
 PROFILE = os.path.join(ROOT, "profiles", "batch_kernel_64x1080p_b64.txt")
+PROFILE_MP64 = os.path.join(ROOT, "profiles", "scan_kernel_8192x8192_b128.txt")
 SCAN_SOURCES = ("ihist_scan.cuh", "ihist_device.cuh")
 
 
@@ -57,10 +58,14 @@ def parse_args():
                          "and the other bin structures (edges, joint RGB)")
     ap.add_argument("--layout", choices=("bin", "pixel", "quad"), default="bin",
                     help="output layout of the timed path (the workload's is bin-major; the others for captures)")
-    ap.add_argument("--serve-seconds", type=float, default=2.0,
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="simulated seconds of the serving workload per server mode (0 = skip)")
     ap.add_argument("--frames", type=int, default=64,
                     help="frames per step (64 = the workload; smaller only for profiler captures)")
+    ap.add_argument("--case", choices=("sequence", "mp64-slice"), default="sequence",
+                    help="mp64-slice: only a few launches of the 8192x8192 x 128-bin scan's launch shape "
+                         "on the top --slice-rows rows (a profiler capture of that kernel at a few GB)")
+    ap.add_argument("--slice-rows", type=int, default=768)
     return ap.parse_args()
 
 
@@ -112,12 +117,12 @@ def scan_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per scan launch from the committed ncu summary, if it was
+def profiled_traffic(path=PROFILE):
+    """DRAM bytes per scan launch from a committed ncu summary, if it was
     taken on the current kernel source; else None."""
     try:
         kv = {}
-        for line in open(PROFILE):
+        for line in open(path):
             if "=" in line and not line.lstrip().startswith("#"):
                 k, v = line.split("=", 1)
                 kv[k.strip()] = v.strip()
@@ -136,16 +141,56 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+class _Nvml:
+    """SM clock, power and clock-event reasons of one GPU read through NVML
+    (the library nvidia-smi itself reads), for sampling every few
+    milliseconds; None where NVML is missing."""
+
+    REASONS = ((0x4, "sw_power_cap"), (0x8, "hw_slowdown"), (0x20, "sw_thermal_slowdown"),
+               (0x40, "hw_thermal_slowdown"), (0x80, "hw_power_brake_slowdown"))
+
+    def __init__(self, bus_id: str):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus_id.encode(), ctypes.byref(self.dev)) != 0:
+            raise OSError("no NVML device at %s" % bus_id)
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        ct = self.ct
+        clk, mx, mw, rs = ct.c_uint(0), ct.c_uint(0), ct.c_uint(0), ct.c_ulonglong(0)
+        if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, ct.byref(clk)) != 0:  # NVML_CLOCK_SM
+            return None
+        self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, ct.byref(mx))
+        self.lib.nvmlDeviceGetPowerUsage(self.dev, ct.byref(mw))
+        self.reasons_fn(self.dev, ct.byref(rs))
+        return clk.value, mx.value, mw.value / 1000.0, rs.value
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """Clocks and throttle reasons during a timed region: NVML every 5 ms in
+    a thread (a timed region of 0.1 s still gets ~20 samples) and nvidia-smi
+    every 200 ms as a cross-check."""
 
     FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self):
+    def __init__(self, nvml_bus_id: str | None = None, period_s: float = 0.005):
         self.proc = None
         self.path = os.path.join(tempfile.gettempdir(), "ihist_clocks_%d.csv" % os.getpid())
+        self.period_s = period_s
+        self.nvml_bus_id = nvml_bus_id
+        self.nvml_rows = []
+        self.thread = None
 
     def start(self):
         try:
@@ -154,10 +199,28 @@ class ClockSampler:
                                           "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
+        if self.nvml_bus_id:
+            import threading
+            try:
+                nv = _Nvml(self.nvml_bus_id)
+            except (OSError, AttributeError):
+                return
+            self.stop_flag = threading.Event()
 
-    def stop(self, bus_id: str | None):
+            def loop():
+                while not self.stop_flag.is_set():
+                    r = nv.sample()
+                    if r is not None:
+                        self.nvml_rows.append(r)
+                    time.sleep(self.period_s)
+                nv.close()
+
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
+
+    def _smi_rows(self, bus_id):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return []
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -176,14 +239,41 @@ class ClockSampler:
             os.remove(self.path)
         except OSError:
             pass
+        return rows
+
+    def stop(self, bus_id: str | None):
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=5)
+        rows = self._smi_rows(bus_id)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        smi_sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        smi_mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        smi_reasons = {n for r in rows for n, v in zip(names, r[6:10]) if v.strip().lower() == "active"}
+        if self.nvml_rows:
+            sm = [float(r[0]) for r in self.nvml_rows]
+            reasons = {n for r in self.nvml_rows for bit, n in _Nvml.REASONS if r[3] & bit} | smi_reasons
+            return {"sm_mhz": statistics.median(sm), "sm_mhz_min": min(sm),
+                    "sm_max_mhz": max(max(r[1] for r in self.nvml_rows), max(smi_mx, default=0.0)),
+                    "reasons": sorted(reasons), "samples": len(self.nvml_rows),
+                    "power_w_max": max(r[2] for r in self.nvml_rows),
+                    "source": "NVML every %.0f ms during the timed region (+ %d nvidia-smi samples at 200 ms)"
+                              % (1000 * self.period_s, len(rows))}
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({n for r in rows for n, v in zip(names, r[6:10]) if v.strip().lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        return {"sm_mhz": statistics.median(smi_sm) if smi_sm else None,
+                "sm_max_mhz": max(smi_mx) if smi_mx else None,
+                "reasons": sorted(smi_reasons), "samples": len(rows), "source": "nvidia-smi every 200 ms"}
+
+
+def nvml_bus_id(dev):
+    """PCI bus id of a torch device in NVML's form (domain:bus:device.0)."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except AttributeError:
+        return None
 
 
 def cpu_baseline(frames: np.ndarray, seconds: float, threads: int) -> dict:
@@ -208,6 +298,39 @@ def host_cores() -> int:
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count() or 1
+
+
+def run_mp64_slice(args) -> int:
+    """The 8192x8192 x 128-bin frame's scan launch shape (the tiling its plan
+    resolves to) on a slice of the frame's top rows: the launches a profiler
+    captures for that workload without holding 32 GiB on the device."""
+    import torch
+
+    from paper_1711_01919_gb300 import build as cuda_build
+    from paper_1711_01919_gb300 import ihist, synth
+    cuda_build.build()
+    ihist.load()
+    h, w, b = args.slice_rows, 8192, 128
+    with ihist.Plan(8192, w, b) as full:
+        tune = dict(full.tune)
+    img = torch.from_numpy(synth.sinusoid_frame(synth.workload_seed(5), 8192, w)[:h].copy()).cuda()
+    out = torch.empty((b, h, w), dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    keep = {k: tune[k] for k in ("rows_per_band", "bins_per_cta", "chunks_per_warp", "groups_per_cta", "ctas_per_sm")}
+    with ihist.Plan(h, w, b, tune=keep) as plan:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * (args.warmup + args.steps))]
+        for k in range(args.warmup + args.steps):
+            ev[2 * k].record()
+            ihist.ihist_compute(plan.handle, img.data_ptr(), w, out.data_ptr(), s)
+            ev[2 * k + 1].record()
+        torch.cuda.synchronize()
+        if plan.status() != ihist.IHIST_OK:
+            raise SystemExit("device status error in the 8192-column slice")
+        ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.warmup, args.warmup + args.steps)]
+        print(json.dumps({"case": "mp64-slice", "rows": h, "W": w, "B": b, "tile": plan.tune,
+                          "full_frame_tile": tune, "launch_ms": ms,
+                          "bytes_per_launch": h * w * b * 4 + h * w}), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -362,21 +485,51 @@ def configs_report(stream, peak: float) -> dict:
     rects = torch.from_numpy(synth.rects(synth.workload_seed(5) + 1, 1 << 20, h, w)).cuda()
     q = torch.empty((1 << 20, b), dtype=torch.int32, device="cuda")
     with ihist.Plan(h, w, b) as plan:
+        clocks = ClockSampler(nvml_bus_id(torch.cuda.current_device()))
+        clocks.start()
         ms = _median_ms(lambda: ihist.ihist_compute(plan.handle, img.data_ptr(), w, out.data_ptr(), s), stream,
                         reps=3, warm=2)
+        clk = clocks.stop(None)
         qms = _median_ms(lambda: ihist.ihist_query(plan.handle, out.data_ptr(), rects.data_ptr(), 1 << 20,
                                                    q.data_ptr(), s), stream, reps=3, warm=2)
         if plan.status() != ihist.IHIST_OK:
             raise SystemExit("device status error in the 8192x8192 run")
         byts = h * w * b * 4 + h * w
         rep["mp64_8192x8192_b128"] = {"scan_ms": ms, "gbs": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak,
-                                      "query_ms_2p20_rects": qms, "tile": plan.tune}
+                                      "bytes_per_launch": byts, "traffic": profiled_traffic(PROFILE_MP64),
+                                      "traffic_source": "ncu DRAM bytes of the same launch shape on the top rows "
+                                                        "of the frame, scaled to 8192 rows (profiles/)",
+                                      "clocks": clk, "query_ms_2p20_rects": qms, "tile": plan.tune}
+        rep["mp64_8192x8192_b128"].update(query_gather_report(out, qms, 1 << 20, b, stream))
     del img, out, rects, q
     torch.cuda.empty_cache()
     rep["host_output_1080p_b64"] = host_output_report(stream, peak)
     rep["window_search_1080p_b64"] = window_search_report(stream)
     rep["paper_mappings_1080p_b64"] = mappings_report(stream, peak)
     return rep
+
+
+def query_gather_report(hist, query_ms: float, nrects: int, nbins: int, stream) -> dict:
+    """The random-gather ceiling of a bin-major region query: 2^26 random
+    4-byte loads over the same 32 GiB histogram (torch.take), timed like the
+    query.  A (rect, bin) pair of Eq. 2 needs four such loads, so the probe
+    bounds the pairs per second any gather-per-corner kernel can reach."""
+    import torch
+    n = 1 << 26
+    g = torch.Generator(device=hist.device)
+    g.manual_seed(1711)
+    idx = torch.randint(0, hist.numel(), (n,), device=hist.device, dtype=torch.int64, generator=g)
+    flat = hist.view(-1)
+    ms = _median_ms(lambda: torch.take(flat, idx), stream, reps=3, warm=2)
+    del idx
+    gathers_per_s = n / (ms / 1e3)
+    pairs = nrects * nbins
+    ceiling_ms = 4 * pairs / gathers_per_s * 1e3
+    return {"gather_probe": {"loads": n, "ms": ms, "loads_per_s": gathers_per_s,
+                             "form": "torch.take of 2^26 uniform random words of the 32 GiB histogram"},
+            "query_pairs": pairs, "query_ms_at_gather_ceiling": ceiling_ms,
+            "query_frac_of_gather_ceiling": ceiling_ms / query_ms,
+            "query_algorithmic_gbs": pairs * 20 / (query_ms / 1e3) / 1e9}
 
 
 def mappings_report(stream, peak: float) -> dict:
@@ -583,6 +736,8 @@ def main():
         NFRAMES = args.frames
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "mp64-slice":
+        return run_mp64_slice(args)
     import torch
     import torch.distributed as dist
 
@@ -633,7 +788,7 @@ def main():
     # ---- device-resident timed region ----
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler()
+    clocks = ClockSampler(nvml_bus_id(dev))
     clocks.start()
     if world > 1:
         dist.barrier()

@@ -156,6 +156,17 @@ int ihist_plan_lut(int h, int w, int nbins, int layout, const int *bin_of_value,
 int ihist_plan_edges(int h, int w, int nbins, int layout, const int *edges,
                      const ihist_tune_t *tune, ihist_plan_t *out);
 
+/* The value -> bin table of bins by edges (Sec. 2.1 leaves the binning Q of
+ * Eq. 1 open; this is the table ihist_plan_edges bins with).  edges: HOST
+ * array of nbins + 1 strictly increasing ints in [0, 256] (1 <= nbins <=
+ * 256); bin_of_value: HOST array of 256 ints, filled with the bin k of each
+ * intensity v, edges[k] <= v < edges[k+1], or -1 for values outside
+ * [edges[0], edges[nbins]).  Pass the table as ihist_frame_t.bin_of_value to
+ * bin a batch frame by edges.  Host-only (no device, no allocation);
+ * IHIST_ERR_INVALID_ARG for a NULL pointer, nbins out of range or edges that
+ * do not increase within [0, 256]. */
+int ihist_edges_table(int nbins, const int *edges, int *bin_of_value);
+
 /* Joint histogram of a multi-channel frame (the higher-dimensional, e.g.
  * colour, histograms of Sec. 1 / Sec. 2.1).  Frames hold `channels` (1..4)
  * interleaved bytes per pixel: pixel (y, x) channel c at

@@ -385,18 +385,25 @@ extern "C" int ihist_plan_lut(int h, int w, int nbins, int layout, const int *bi
   return plan_create(h, w, nbins, layout, tune, bin_of_value, nullptr, out);
 }
 
-extern "C" int ihist_plan_edges(int h, int w, int nbins, int layout, const int *edges,
-                                const ihist_tune_t *tune, ihist_plan_t *out) {
-  if (!edges || nbins < 1 || nbins > 256) return IHIST_ERR_INVALID_ARG;
+extern "C" int ihist_edges_table(int nbins, const int *edges, int *bin_of_value) {
+  if (!edges || !bin_of_value || nbins < 1 || nbins > 256) return IHIST_ERR_INVALID_ARG;
   if (edges[0] < 0 || edges[nbins] > 256) return IHIST_ERR_INVALID_ARG;
   for (int k = 0; k < nbins; ++k)
     if (edges[k] >= edges[k + 1]) return IHIST_ERR_INVALID_ARG;
-  int table[256];
+  // bin k holds edges[k] <= v < edges[k + 1]; v walks up once, k with it
   int k = 0;
   for (int v = 0; v < 256; ++v) {
     while (k < nbins && v >= edges[k + 1]) ++k;
-    table[v] = (k < nbins && v >= edges[k]) ? k : -1;
+    bin_of_value[v] = (k < nbins && v >= edges[k]) ? k : -1;
   }
+  return IHIST_OK;
+}
+
+extern "C" int ihist_plan_edges(int h, int w, int nbins, int layout, const int *edges,
+                                const ihist_tune_t *tune, ihist_plan_t *out) {
+  int table[256];
+  const int rc = ihist_edges_table(nbins, edges, table);
+  if (rc != IHIST_OK) return rc;
   return ihist_plan_lut(h, w, nbins, layout, table, tune, out);
 }
 

@@ -40,7 +40,7 @@ EXPORTED = (
     "ihist_batch_items", "ihist_batch_destroy", "ihist_batch_query_all", "ihist_batch_upload_compute",
     "ihist_compute_noalloc", "ihist_plan_lut", "ihist_plan_edges", "ihist_plan_joint",
     "ihist_plan_channels", "ihist_window_search", "ihist_mapping_workspace_bytes", "ihist_mapping_compute",
-    "ihist_batch_get_tune",
+    "ihist_batch_get_tune", "ihist_edges_table",
 )
 
 
@@ -149,6 +149,8 @@ def load(path: str = LIB_PATH):
         L.ihist_plan_lut.restype = ci
         L.ihist_plan_edges.argtypes = [ci, ci, ci, ci, ip, tp, ctypes.POINTER(vp)]
         L.ihist_plan_edges.restype = ci
+        L.ihist_edges_table.argtypes = [ci, ip, ip]
+        L.ihist_edges_table.restype = ci
         L.ihist_plan_joint.argtypes = [ci, ci, ci, ip, ci, tp, ctypes.POINTER(vp)]
         L.ihist_plan_joint.restype = ci
         L.ihist_mapping_workspace_bytes.argtypes = [ci, ci, ci, ci]
@@ -343,16 +345,16 @@ def _frames_array(frames):
 
 
 def edges_table(edges):
-    """Value -> bin table of bins by edges: bin k holds edges[k] <= v <
-    edges[k + 1]; values outside [edges[0], edges[-1]) are in no bin (-1)."""
+    """Value -> bin table of bins by edges (ihist_edges_table): bin k holds
+    edges[k] <= v < edges[k + 1]; values outside [edges[0], edges[-1]) are in
+    no bin (-1).  ValueError for edges that do not increase within [0, 256]."""
     e = [int(x) for x in edges]
-    if len(e) < 2 or any(b <= a for a, b in zip(e, e[1:])) or e[0] < 0 or e[-1] > 256:
+    out = (ctypes.c_int * 256)()
+    code = load().ihist_edges_table(len(e) - 1, _ints(e) if e else None, out)
+    if code == IHIST_ERR_INVALID_ARG:
         raise ValueError("edges must increase strictly within [0, 256]")
-    table = [-1] * 256
-    for k in range(len(e) - 1):
-        for v in range(e[k], e[k + 1]):
-            table[v] = k
-    return table
+    _check(code, "ihist_edges_table")
+    return list(out)
 
 
 def ihist_batch_plan(frames, tune=None) -> int:

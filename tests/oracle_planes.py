@@ -1,21 +1,32 @@
 """Worker side of the full-size plane comparison in test_gpu_large.py: each
 worker process computes oracle bin planes of the 8192 x 8192 frame (one
-independent run of Algorithm 1 per plane) and returns their SHA-256
-digests.  Imports nothing but numpy and the oracle, so spawned workers start
+independent run of Algorithm 1 per plane) and the oracle's Eq. 2 region
+counts of that bin for every query rectangle, and returns SHA-256 digests of
+both.  Imports nothing but numpy and the oracle, so spawned workers start
 quickly."""
 import hashlib
+
+import numpy as np
 
 import oracle
 
 _IMG = None
+_RECTS = None
 
 
-def init(img):
-    global _IMG
+def init(img, rects=None):
+    global _IMG, _RECTS
     _IMG = img
+    _RECTS = rects
 
 
 def plane_digest(args):
+    """(k, digest of oracle plane k, digest of its query column or None)."""
     nbins, k = args
     ref = oracle.integral_histogram_plane(_IMG, nbins, k)
-    return k, hashlib.sha256(ref.tobytes() if not ref.flags.c_contiguous else ref).hexdigest()
+    d_plane = hashlib.sha256(np.ascontiguousarray(ref)).hexdigest()
+    d_query = None
+    if _RECTS is not None:
+        col = np.ascontiguousarray(oracle.query(ref[None], _RECTS)[:, 0], dtype=np.uint32)
+        d_query = hashlib.sha256(col).hexdigest()
+    return k, d_plane, d_query

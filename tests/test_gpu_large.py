@@ -6,8 +6,10 @@ an independent run of Algorithm 1), and every one of the 128 planes against
 the oracle's by SHA-256 digest (the planes computed in parallel on the host
 cores); every word through the second-difference
 property (Algorithm 1 solved for Q: the 2-D second difference of H is the
-one-hot of the pixel's bin); 2^20 region queries against the oracle's Eq. 2 on
-the sampled planes, and per-rectangle totals equal to the rectangle's area.
+one-hot of the pixel's bin); the 2^20 region queries against the oracle's
+Eq. 2 word for word on the sampled bins and by digest of each bin's column on
+all 128 bins (bins from 64 up sit past element offset 2^32 of H), and
+per-rectangle totals equal to the rectangle's area.
 """
 import concurrent.futures as cf
 import hashlib
@@ -65,25 +67,37 @@ def test_sampled_plane_vs_oracle(big, k):
     assert np.array_equal(got, ref), "plane %d: %d words differ" % (k, int((got != ref).sum()))
 
 
-def test_every_plane_vs_oracle_by_digest(big):
-    # all 128 planes (32 GiB): the oracle computes every plane in spawned
-    # host processes while the GPU planes are copied back and hashed in
-    # threads; equal SHA-256 digests per plane mean equal words.  A worker
-    # that dies breaks the pool with an error (no silent wait).
-    img, _, _, out, _, _, _ = big
+@pytest.fixture(scope="module")
+def oracle_digests(big):
+    """{bin: (plane digest, query-column digest)} of the oracle, all 128 bins.
+
+    The oracle computes every plane (and Eq. 2 on it for every rectangle) in
+    spawned host processes; a worker that dies breaks the pool with an error
+    (no silent wait)."""
+    img, rects = big[0], big[1]
     oracle.default()  # the oracle library exists before any worker loads it
     nproc = max(1, min(16, os.cpu_count() or 1))
     with cf.ProcessPoolExecutor(nproc, mp_context=multiprocessing.get_context("spawn"),
-                                initializer=oracle_planes.init, initargs=(img,)) as pool:
+                                initializer=oracle_planes.init, initargs=(img, rects)) as pool:
         pending = [pool.submit(oracle_planes.plane_digest, (NBINS, k)) for k in range(NBINS)]
+        ref = {}
+        for f in pending:
+            k, dp, dq = f.result(timeout=1800)
+            ref[k] = (dp, dq)
+    return ref
 
-        def gpu_digest(k):
-            return k, hashlib.sha256(out[k].cpu().numpy()).hexdigest()
 
-        with cf.ThreadPoolExecutor(8) as ex:
-            got = dict(ex.map(gpu_digest, range(NBINS)))
-        ref = dict(f.result(timeout=1200) for f in pending)
-    bad = [k for k in range(NBINS) if got[k] != ref[k]]
+def test_every_plane_vs_oracle_by_digest(big, oracle_digests):
+    # all 128 planes (32 GiB): the GPU planes are copied back and hashed in
+    # threads; equal SHA-256 digests per plane mean equal words.
+    img, _, _, out, _, _, _ = big
+
+    def gpu_digest(k):
+        return k, hashlib.sha256(out[k].cpu().numpy()).hexdigest()
+
+    with cf.ThreadPoolExecutor(8) as ex:
+        got = dict(ex.map(gpu_digest, range(NBINS)))
+    bad = [k for k in range(NBINS) if got[k] != oracle_digests[k][0]]
     if bad:
         k = bad[0]
         plane = out[k].cpu().numpy().view(np.uint32)
@@ -119,8 +133,18 @@ def test_queries(big):
     img, rects, _, out, d_rects, q, _ = big
     area = ((d_rects[:, 2] - d_rects[:, 0] + 1).to(torch.int64) * (d_rects[:, 3] - d_rects[:, 1] + 1))
     assert torch.equal(q.to(torch.int64).sum(1), area)
-    for k in SAMPLE_PLANES[:3]:
+    for k in SAMPLE_PLANES:  # 64, 101 and 127 read H past element offset 2^32
         ref_plane = oracle.integral_histogram_plane(img, NBINS, k)
         ref_q = oracle.query(ref_plane[None], rects)[:, 0]
         got = q[:, k].cpu().numpy().view(np.uint32)
         assert np.array_equal(got, ref_q), "bin %d" % k
+
+
+def test_queries_every_bin_vs_oracle_by_digest(big, oracle_digests):
+    q = big[5]
+    bad = []
+    for k in range(NBINS):
+        col = np.ascontiguousarray(q[:, k].cpu().numpy().view(np.uint32))
+        if hashlib.sha256(col).hexdigest() != oracle_digests[k][1]:
+            bad.append(k)
+    assert not bad, "query columns of %d bins differ from the oracle's Eq. 2, first bin %d" % (len(bad), bad[0])

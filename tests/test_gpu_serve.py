@@ -1,9 +1,12 @@
-"""Served results equal results computed alone, word for word: each frame's
-resident histogram and each query's rows, in the batched (continuous
-batching) and the plain server, with small pools of distinct frames."""
+"""Served results against the oracle and against results computed alone,
+word for word: each frame's resident histogram (Eq. 1, Algorithm 1), each
+query's rows (Eq. 2) and each search's best window, in the batched
+(continuous batching) and the plain server, with small pools of distinct
+frames."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1711_01919_gb300 import ihist, serve, synth
 
 pytestmark = pytest.mark.gpu
@@ -72,6 +75,42 @@ def check_alone(srv, reqs):
     return nq
 
 
+def check_oracle(srv, reqs):
+    """Every resident histogram, query row and search answer against the
+    oracle computed from the request's own host frame.  Frames of the pool
+    repeat, so the oracle runs once per (frame, bin count)."""
+    frames = {r.rid: r for r in reqs if isinstance(r, serve.FrameRequest)}
+    groups = {}
+    for rid in srv.store.resident():
+        r = frames[rid]
+        groups.setdefault((id(r.frame), r.nbins), []).append(rid)
+    nq = 0
+    for (_, nbins), rids in groups.items():
+        img = frames[rids[0]].frame.numpy()
+        ref = oracle.integral_histogram(img, nbins)
+        for rid in rids:
+            got = srv.store.payload(rid)[0].cpu().numpy().view(np.uint32).reshape(ref.shape)
+            assert np.array_equal(got, ref), "frame %d differs from the oracle" % rid
+        for q in reqs:
+            if q.rid not in srv.results or getattr(q, "target", None) not in rids:
+                continue
+            if isinstance(q, serve.QueryRequest):
+                want = oracle.query(ref, np.ascontiguousarray(q.rects))
+                got = srv.results[q.rid].numpy().view(np.uint32).reshape(want.shape)
+                assert np.array_equal(got, want), "query %d differs from the oracle" % q.rid
+                nq += 1
+            elif isinstance(q, serve.SearchRequest):
+                rect = np.array([[q.x, q.y, q.x + q.win_w - 1, q.y + q.win_h - 1]], dtype=np.int32)
+                target = oracle.query(ref, rect)[0]
+                scores = oracle.window_intersection(img, nbins, target, q.win_h, q.win_w, q.stride)
+                i = int(np.argmax(scores))
+                nx = scores.shape[1]
+                assert serve.decode_best(int(srv.results[q.rid].item()), nx) == (int(scores.flat[i]), i // nx, i % nx), \
+                    "search %d differs from the oracle" % q.rid
+                nq += 1
+    return nq
+
+
 @pytest.mark.parametrize("mode", ["batched", "plain"])
 def test_served_results_equal_alone(mode):
     srv, ex, reqs = run_server(mode)
@@ -83,6 +122,7 @@ def test_served_results_equal_alone(mode):
     assert all(d.status == "ok" or d.t_arrival < first_ready for d in done if d.kind == "query")
     nq = check_alone(srv, reqs)
     assert nq >= 3
+    assert check_oracle(srv, reqs) == nq
     ex.close()
 
 
@@ -91,5 +131,5 @@ def test_batched_server_under_a_small_budget_evicts_and_stays_exact():
     assert srv.store.evicted > 0
     assert srv.store.used <= 1 << 30
     assert all(d.status == "ok" for d in srv.done if d.kind == "frame")
-    check_alone(srv, reqs)
+    assert check_alone(srv, reqs) == check_oracle(srv, reqs)
     ex.close()
