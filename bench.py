@@ -376,13 +376,16 @@ def serving_report(seconds: float) -> dict:
     faster than they can be served."""
     from paper_1711_01919_gb300 import serve
 
-    keep = ("completed", "rejected", "p50_ms", "p99_ms", "per_s")
+    keep = ("completed", "rejected", "p50_ms", "p99_ms", "per_s", "launch_wait_p99_ms")
     out = {"workload": "Poisson arrivals for %.1f s: frames at 2000/s (320x240..1920x1080, 16-64 bins), "
                        "queries of 10,000 rects at 200/s and searches for a 64x64 patch (stride 8) at 50/s "
                        "against a random resident histogram; 40 GB budget, LRU eviction" % seconds}
     for mode in ("batched", "plain"):
         rep = serve.serve(mode=mode, duration_s=seconds)
         out[mode] = {k: {f: rep[k][f] for f in keep} for k in ("frame", "query", "search")}
+        out[mode]["frame"]["by_path"] = rep["frame"]["by_path"]
+        out[mode]["launch_sizes"] = rep["launch_sizes"]
+        out[mode]["host_issue_p50_ms"] = rep["host_issue_p50_ms"]
         out[mode]["evicted"] = rep["evicted"]
     for mode in ("batched", "plain"):
         rep = serve.serve(mode=mode, duration_s=seconds / 4, saturate=True)
@@ -492,6 +495,19 @@ def configs_report(stream, peak: float) -> dict:
         clk = clocks.stop(None)
         qms = _median_ms(lambda: ihist.ihist_query(plan.handle, out.data_ptr(), rects.data_ptr(), 1 << 20,
                                                    q.data_ptr(), s), stream, reps=3, warm=2)
+        sorted_ms = {}
+        work = torch.empty((plan.query_work_bytes(1 << 20, 4),), dtype=torch.uint8, device="cuda")
+        for bpp in (4, 8, 16):
+            if work.numel() < plan.query_work_bytes(1 << 20, bpp):
+                work = torch.empty((plan.query_work_bytes(1 << 20, bpp),), dtype=torch.uint8, device="cuda")
+            q2 = torch.empty_like(q)
+            sorted_ms[bpp] = _median_ms(lambda: ihist.ihist_query_sorted(
+                plan.handle, out.data_ptr(), rects.data_ptr(), 1 << 20, q2.data_ptr(), bpp, work.data_ptr(),
+                work.numel(), s), stream, reps=3, warm=2)
+            if not torch.equal(q2, q):
+                raise SystemExit("sorted and plain 8192x8192 queries differ")
+            del q2
+        del work
         if plan.status() != ihist.IHIST_OK:
             raise SystemExit("device status error in the 8192x8192 run")
         byts = h * w * b * 4 + h * w
@@ -499,7 +515,10 @@ def configs_report(stream, peak: float) -> dict:
                                       "bytes_per_launch": byts, "traffic": profiled_traffic(PROFILE_MP64),
                                       "traffic_source": "ncu DRAM bytes of the same launch shape on the top rows "
                                                         "of the frame, scaled to 8192 rows (profiles/)",
-                                      "clocks": clk, "query_ms_2p20_rects": qms, "tile": plan.tune}
+                                      "clocks": clk, "query_ms_2p20_rects": qms,
+                                      "query_sorted_ms_2p20_rects": {"bins_per_pass_%d" % k: v
+                                                                     for k, v in sorted_ms.items()},
+                                      "tile": plan.tune}
         rep["mp64_8192x8192_b128"].update(query_gather_report(out, qms, 1 << 20, b, stream))
     del img, out, rects, q
     torch.cuda.empty_cache()

@@ -79,8 +79,9 @@ typedef struct ihist_plan_s *ihist_plan_t;
  *   chunks_per_warp m, 128-column chunks one warp owns (1, 2, 4 or 8;
  *                   at most 2 with bins_per_cta 16)
  *   groups_per_cta  bin groups one CTA serves side by side (warps = groups
- *                   x ceil(ceil(w/128)/m), at most 16 in all); narrow frames
- *                   fill a CTA this way
+ *                   x ceil(ceil(w/128)/m), at most 16 in all; frames split
+ *                   into width segments count the warps of one segment);
+ *                   narrow frames fill a CTA this way
  *   ctas_per_sm     persistent grid = ctas_per_sm x SMs (0 = occupancy limit)
  *   timeout_us      limit of each carry wait before it gives up and latches
  *                   IHIST_ERR_LOOKBACK_TIMEOUT (default 2,000,000 us)
@@ -92,8 +93,8 @@ typedef struct ihist_plan_s *ihist_plan_t;
  *   warps_per_cta   batched launches: warps per CTA (4, 8 or 16; default
  *                   8, or 16 for pixel-major batches with 8 bins per CTA
  *                   and for frames wider than 8 warps can cover).  A frame
- *                   needs ceil(w/128) <= 4 x warps_per_cta (2 x with 16
- *                   bins per CTA).
+ *                   wider than 4 x warps_per_cta chunks of 128 columns (2 x
+ *                   with 16 bins per CTA) is split into width segments.
  *                   Plans derive it from the tiling, ignore it on input
  *                   and report it in ihist_plan_get_tune.
  *   overlap         plans: every ihist_compute (and ihist_query) is launched
@@ -128,8 +129,12 @@ typedef struct {
 
 /* Create a plan for frames of h rows x w columns and nbins bins in the given
  * layout, with default tiling.  Limits: 1 <= h, w <= 65535, h*w < 2^32,
- * 1 <= nbins <= 256, w <= 16384.  Allocates the plan's device workspace on the
- * current device.  *out is set only on IHIST_OK. */
+ * 1 <= nbins <= 256.  A frame wider than one CTA's warps cover (16 warps x
+ * chunks_per_warp x 128 columns) has each band split into width segments of
+ * equal chunk counts, one work item each; a segment adds the per-row bin
+ * totals that the segments to its left publish right after counting (Eq. 1's
+ * row sums split at the segment edges).  Allocates the plan's device
+ * workspace on the current device.  *out is set only on IHIST_OK. */
 int ihist_plan(int h, int w, int nbins, int layout, ihist_plan_t *out);
 
 /* As ihist_plan with explicit tiling (NULL = defaults). */
@@ -225,6 +230,30 @@ int ihist_compute(ihist_plan_t plan, const uint8_t *d_in, size_t in_pitch, uint3
  * waits for that kernel before reading anything. */
 int ihist_query(ihist_plan_t plan, const uint32_t *d_hist, const int32_t *d_rects, int n,
                 uint32_t *d_hist_out, void *stream);
+
+/* Region histograms by Eq. 2 for large batches of rectangles on a bin-major
+ * H, with the corner lookups put in row order first (same results as
+ * ihist_query, word for word).  ihist_query reads each corner word where it
+ * lies, so random rectangles on a large bin-major H cost one DRAM line per
+ * 4-byte corner; here the corners of all n rectangles are bucketed by row
+ * (a counting sort, once per call), then each group of bins_per_pass bins
+ * reads them bucket by bucket, so the corners of a row share the lines they
+ * fall on, and a second pass combines each rectangle's four corners.
+ *   bins_per_pass  bins gathered per pass: 4, 8 or 16 (0 = 8)
+ *   d_work         device scratch of ihist_query_work_bytes(plan, n,
+ *                  bins_per_pass) bytes, 256-byte aligned, owned by the
+ *                  caller; about 32 + 16 * bins_per_pass bytes per rectangle
+ *                  plus 8 per frame row.  Its contents need not be kept
+ *                  between calls; two calls sharing it must not overlap.
+ * Other arguments and the bad-rectangle rule as for ihist_query.  Bin-major
+ * plans only (IHIST_ERR_UNSUPPORTED otherwise); n < 2^29;
+ * IHIST_ERR_INVALID_ARG if work_bytes is too small.  Five kinds of launch on
+ * `stream` (count, offsets, scatter, then a gather and a combine per group
+ * of bins); allocates nothing. */
+size_t ihist_query_work_bytes(ihist_plan_t plan, int n, int bins_per_pass);
+int ihist_query_sorted(ihist_plan_t plan, const uint32_t *d_hist, const int32_t *d_rects, int n,
+                       uint32_t *d_hist_out, int bins_per_pass, void *d_work, size_t work_bytes,
+                       void *stream);
 
 /* Sliding-window histogram search over a resident integral histogram (the
  * detection / tracking use of Sec. 1).  Window (i, j) covers rows
@@ -335,8 +364,8 @@ typedef struct {
  * default 4, or 16 / 8 when a frame is pixel-major), rows_per_band and
  * warps_per_cta apply to every frame; chunks per warp and groups per CTA
  * are chosen per frame to fill the CTA's warps.  Frames wider than
- * 4 x warps_per_cta chunks of 128 columns (2 x with 16 bins per CTA) give
- * IHIST_ERR_UNSUPPORTED (at most 8192 columns with 16 warps).  Frames bound
+ * 4 x warps_per_cta chunks of 128 columns (2 x with 16 bins per CTA) are
+ * split into width segments as in ihist_plan.  Frames bound
  * later by ihist_batch_set_io keep within the launch shape the planned
  * frames fixed (chunks per warp, carry width per CTA), which may leave some
  * of a narrower frame's CTA idle.  If any planned frame has a bin table

@@ -17,6 +17,7 @@
 #include "ihist_joint.cuh"
 #include "ihist_kernels.h"
 #include "ihist_query.cuh"
+#include "ihist_query_sorted.cuh"
 #include "ihist_window.cuh"
 
 using namespace ihist;
@@ -50,6 +51,7 @@ struct ihist_plan_s {
   uint8_t *idx;         // kJoint: joint-bin plane [H][idx_pitch]
   size_t idx_pitch;
   int R, G, m, NW, nbands, ngroups, nchunks, wpg, gpc, ngsets;
+  int nsegs, cps;       // width segments per band and chunks per segment
   unsigned int nitems;
   int ctas_per_sm;
   unsigned int timeout_us;
@@ -62,6 +64,7 @@ struct ihist_plan_s {
   Ctrl *ctrl_alt;  // control block of every other launch (epochs of the other parity)
   unsigned long long launches;
   uint32_t *flags, *agg_cnt, *agg_left, *incl;
+  uint32_t *hflags, *hagg;     // width segments (nsegs > 1): flags and per-row totals
   cudaEvent_t ev_uploaded[2];  // sequence pipeline: slot filled
   cudaEvent_t ev_consumed[2];  // sequence pipeline: slot read by its compute
   cudaEvent_t ev_queried;      // sequence pipeline: a frame's query rows are in d_query
@@ -101,7 +104,6 @@ int ihist::host::validate_shape(int h, int w, int nbins, int layout) {
   if (layout != IHIST_BIN_MAJOR && layout != IHIST_PIXEL_MAJOR && layout != IHIST_QUAD_MAJOR)
     return IHIST_ERR_INVALID_ARG;
   if (layout == IHIST_QUAD_MAJOR && nbins % 4 != 0) return IHIST_ERR_INVALID_ARG;
-  if (w > 16384) return IHIST_ERR_UNSUPPORTED;
   return IHIST_OK;
 }
 
@@ -148,7 +150,7 @@ static int occupancy(ScanFn fn, int threads, size_t smem) {
 // last partial wave) x (1 - carry overhead, about 1.25/R of the output
 // bytes) x (warps per SM, up to 24) x (fraction of CTA bin groups in use).
 // Fields the caller fixed (non-zero) are kept.
-static void default_tiling(int h, int ngroups, int wpg, int G, int nchunks, int sms, ScanFn fn,
+static void default_tiling(int h, int ngroups, int wpg, int G, int ncl, int nsegs, int sms, ScanFn fn,
                            size_t optin, int layout, int *R, int *gpc) {
   double best = -1.0;
   int best_r = *R ? *R : std::min(h, 8), best_g = *gpc ? *gpc : 1;
@@ -160,12 +162,12 @@ static void default_tiling(int h, int ngroups, int wpg, int G, int nchunks, int 
     const double used = (double)ngroups / (double)(ngsets * gp);
     const int r_lo = *R ? *R : std::min(h, 8), r_hi = *R ? *R : std::min(h, 255);
     for (int r = r_lo; r <= r_hi; ++r) {
-      const size_t smem = smem_layout(NW, r, G, nchunks * gp, pm_staged(layout, G)).bytes;
+      const size_t smem = smem_layout(NW, r, G, ncl * gp, pm_staged(layout, G)).bytes;
       if (smem > optin) break;
       const int occ = occupancy(fn, NW * 32, smem);
       if (occ < 1) break;
       const long long slots = (long long)occ * sms;
-      const long long items = (long long)((h + r - 1) / r) * ngsets;
+      const long long items = (long long)((h + r - 1) / r) * ngsets * nsegs;
       const long long waves = (items + slots - 1) / slots;
       const double fill = (double)items / (double)(waves * slots);
       const double carry = 1.0 - 1.25 / r;
@@ -189,13 +191,13 @@ static void default_tiling(int h, int ngroups, int wpg, int G, int nchunks, int 
   if (!*R && best_r == std::min(h, 8)) {
     const int NW = best_g * wpg;
     const int ngsets = (ngroups + best_g - 1) / best_g;
-    const size_t smem0 = smem_layout(NW, best_r, G, nchunks * best_g, pm_staged(layout, G)).bytes;
+    const size_t smem0 = smem_layout(NW, best_r, G, ncl * best_g, pm_staged(layout, G)).bytes;
     const long long slots0 = (long long)occupancy(fn, NW * 32, smem0) * sms;
-    if ((long long)((h + best_r - 1) / best_r) * ngsets <= slots0) {
+    if ((long long)((h + best_r - 1) / best_r) * ngsets * nsegs <= slots0) {
       double best_t = 1e30;
       int pick = best_r;
       for (int r = std::min(h, 8); r <= std::min(h, 255); ++r) {
-        const size_t smem = smem_layout(NW, r, G, nchunks * best_g, pm_staged(layout, G)).bytes;
+        const size_t smem = smem_layout(NW, r, G, ncl * best_g, pm_staged(layout, G)).bytes;
         if (smem > optin || occupancy(fn, NW * 32, smem) < 1) break;
         const double t = r + 0.5 * ((h + r - 1) / r);
         if (t < best_t) {
@@ -246,10 +248,18 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   // staged 159 us).
   const bool pm_wide = layout == IHIST_PIXEL_MAJOR && nbins >= 16 && nchunks <= 32 && !table;
   if (t.bins_per_cta == 0) t.bins_per_cta = layout == IHIST_PIXEL_MAJOR ? (pm_wide ? 16 : 8) : 4;
-  if (t.chunks_per_warp == 0)
+  if (t.chunks_per_warp == 0) {
     t.chunks_per_warp = nchunks <= 16 ? 1 : nchunks <= 32 ? 2 : nchunks <= 64 ? 4 : 8;
+    if (t.bins_per_cta == 16) t.chunks_per_warp = std::min(t.chunks_per_warp, 2);  // the 16-bin kernels' limit
+  }
   if (t.timeout_us == 0) t.timeout_us = kDefaultTimeoutUs;
-  const int wpg = (nchunks + t.chunks_per_warp - 1) / t.chunks_per_warp;
+  // Frames wider than 16 warps x m chunks split each band into width
+  // segments of equal chunk counts, one work item each (see the scan kernel).
+  const int wpg_all = (nchunks + t.chunks_per_warp - 1) / t.chunks_per_warp;
+  const int nsegs = (wpg_all + 15) / 16;
+  const int wpg = (wpg_all + nsegs - 1) / nsegs;
+  const int cps = wpg * t.chunks_per_warp;
+  const int ncl = std::min(nchunks, cps);  // chunks of one CTA's group
   const int mmax = mmax_for(t.chunks_per_warp);
   if (wpg * std::max(1, t.groups_per_cta) > 16 || !scan_fn(t.bins_per_cta, mmax, true, true, table))
     return IHIST_ERR_UNSUPPORTED;
@@ -260,7 +270,7 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   const int ngroups = (nbins + t.bins_per_cta - 1) / t.bins_per_cta;
   if (t.groups_per_cta > ngroups) t.groups_per_cta = ngroups;
   if (t.rows_per_band == 0 || t.groups_per_cta == 0)
-    default_tiling(h, ngroups, wpg, t.bins_per_cta, nchunks, sms, fn, optin, layout, &t.rows_per_band,
+    default_tiling(h, ngroups, wpg, t.bins_per_cta, ncl, nsegs, sms, fn, optin, layout, &t.rows_per_band,
                    &t.groups_per_cta);
 
   ihist_plan_s *p = new (std::nothrow) ihist_plan_s;
@@ -284,11 +294,17 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   p->nbands = (h + p->R - 1) / p->R;
   p->ngroups = ngroups;
   p->ngsets = (ngroups + p->gpc - 1) / p->gpc;
-  p->nitems = (unsigned int)p->nbands * (unsigned int)p->ngsets;
+  p->nsegs = nsegs;
+  p->cps = nsegs > 1 ? cps : nchunks;
+  if ((unsigned long long)p->nbands * p->ngsets * nsegs >= 0xffffffffull) {
+    delete p;
+    return IHIST_ERR_UNSUPPORTED;
+  }
+  p->nitems = (unsigned int)p->nbands * (unsigned int)p->ngsets * (unsigned int)nsegs;
   p->timeout_us = t.timeout_us;
   p->fault_skip_band = t.fault_skip_band >= 1 ? t.fault_skip_band - 1 : -1;  // 1-based in the tune struct
   p->overlap = t.overlap;
-  p->smem_bytes = smem_layout(p->NW, p->R, p->G, p->nchunks * p->gpc, pm_staged(layout, p->G)).bytes;
+  p->smem_bytes = smem_layout(p->NW, p->R, p->G, ncl * p->gpc, pm_staged(layout, p->G)).bytes;
   const int occ = p->smem_bytes <= optin ? occupancy(fn, p->NW * 32, p->smem_bytes) : 0;
   if (occ < 1) {
     delete p;
@@ -305,12 +321,17 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   off = align_up(off + sizeof(Ctrl), 256);
   const size_t o_flags = off;
   off = align_up(off + nci * sizeof(uint32_t), 256);
+  const size_t nhs = nsegs > 1 ? (size_t)p->nbands * p->ngroups * nsegs : 0;  // segment records
+  const size_t o_hflags = off;
+  off = align_up(off + nhs * sizeof(uint32_t), 256);
   const size_t o_cnt = off;
   off = align_up(off + nci * kChunk * (p->G / 4) * sizeof(uint32_t), 256);
   const size_t o_left = off;
   off = align_up(off + nci * p->G * sizeof(uint32_t), 256);
   const size_t o_incl = off;
   off = align_up(off + nci * p->G * kChunk * sizeof(uint32_t), 256);
+  const size_t o_hagg = off;
+  off = align_up(off + nhs * ((size_t)p->R * p->G + p->G) * sizeof(uint32_t), 256);
   const size_t o_lut = off;
   if (table) off = align_up(off + 256 * sizeof(uint32_t), 256);
   const size_t o_idx = off;
@@ -329,6 +350,10 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   p->agg_cnt = reinterpret_cast<uint32_t *>(base + o_cnt);
   p->agg_left = reinterpret_cast<uint32_t *>(base + o_left);
   p->incl = reinterpret_cast<uint32_t *>(base + o_incl);
+  if (nhs) {
+    p->hflags = reinterpret_cast<uint32_t *>(base + o_hflags);
+    p->hagg = reinterpret_cast<uint32_t *>(base + o_hagg);
+  }
   if (table) p->lut = reinterpret_cast<uint32_t *>(base + o_lut);
   if (joint) p->idx = reinterpret_cast<uint8_t *>(base + o_idx);
   uint32_t host_lut[256];
@@ -563,6 +588,10 @@ static int compute_frame(ihist_plan_s *p, const uint8_t *d_in, size_t in_pitch, 
   f.agg_left = p->agg_left;
   f.incl = p->incl;
   f.flags = p->flags;
+  f.nsegs = p->nsegs;
+  f.cps = p->cps;
+  f.hagg = p->hagg;
+  f.hflags = p->hflags;
   const unsigned int grid =
       std::min<unsigned int>(p->nitems, (unsigned int)(p->ctas_per_sm * p->sms));
   ScanFn fn = scan_fn(p->G, mmax_for(p->m), tm != nullptr, vec, p->binning == kTable);
@@ -635,6 +664,94 @@ extern "C" int ihist_query(ihist_plan_t p, const uint32_t *d_hist, const int32_t
   if (rc != IHIST_OK) return rc;
   return launch_query(p->H, p->W, p->B, p->layout, p->sms, p->ctrl, d_hist, d_rects, n, d_hist_out,
                       stream);
+}
+
+// Scratch of ihist_query_sorted: row counts (zero between calls), row
+// offsets, the corners' (y, x) in row order, each rectangle's four corner
+// positions and the gathered corner values of one bin group.
+struct SortedQueryWork {
+  size_t o_cnt, o_off, o_pts, o_slot, o_val, bytes;
+};
+
+static SortedQueryWork sorted_query_work(int H, size_t n, int nb) {
+  SortedQueryWork w;
+  size_t off = 0;
+  w.o_cnt = off;
+  off = align_up(off + (size_t)H * 4, 256);
+  w.o_off = off;
+  off = align_up(off + ((size_t)H + 1) * 4, 256);
+  w.o_pts = off;
+  off = align_up(off + 4 * n * 4, 256);
+  w.o_slot = off;
+  off = align_up(off + n * 16, 256);
+  w.o_val = off;
+  off = align_up(off + 4 * n * (size_t)nb * 4, 256);
+  w.bytes = off;
+  return w;
+}
+
+static int sorted_group(int bins_per_pass) { return bins_per_pass == 0 ? 8 : bins_per_pass; }
+
+extern "C" size_t ihist_query_work_bytes(ihist_plan_t p, int n, int bins_per_pass) {
+  if (!p || n < 0 || (bins_per_pass != 0 && bins_per_pass != 4 && bins_per_pass != 8 && bins_per_pass != 16))
+    return 0;
+  return sorted_query_work(p->H, (size_t)n, sorted_group(bins_per_pass)).bytes;
+}
+
+extern "C" int ihist_query_sorted(ihist_plan_t p, const uint32_t *d_hist, const int32_t *d_rects, int n,
+                                  uint32_t *d_hist_out, int bins_per_pass, void *d_work, size_t work_bytes,
+                                  void *stream) {
+  if (!p || n < 0) return IHIST_ERR_INVALID_ARG;
+  if (bins_per_pass != 0 && bins_per_pass != 4 && bins_per_pass != 8 && bins_per_pass != 16)
+    return IHIST_ERR_INVALID_ARG;
+  if (n == 0) return IHIST_OK;
+  if (!d_hist || !d_rects || !d_hist_out || !d_work) return IHIST_ERR_INVALID_ARG;
+  if (((uintptr_t)d_hist & 3u) || ((uintptr_t)d_rects & 3u) || ((uintptr_t)d_hist_out & 3u) ||
+      ((uintptr_t)d_work & 255u))
+    return IHIST_ERR_INVALID_ARG;
+  if (p->layout != IHIST_BIN_MAJOR) return IHIST_ERR_UNSUPPORTED;
+  if ((unsigned long long)n * (unsigned long long)p->B > 0x7fffffffull || (unsigned long long)n >= (1ull << 29))
+    return IHIST_ERR_UNSUPPORTED;
+  const int nb = sorted_group(bins_per_pass);
+  const SortedQueryWork w = sorted_query_work(p->H, (size_t)n, nb);
+  if (work_bytes < w.bytes) return IHIST_ERR_INVALID_ARG;
+  int rc = check_device(p);
+  if (rc != IHIST_OK) return rc;
+  char *base = static_cast<char *>(d_work);
+  unsigned int *cnt = reinterpret_cast<unsigned int *>(base + w.o_cnt);
+  unsigned int *off = reinterpret_cast<unsigned int *>(base + w.o_off);
+  uint32_t *pts = reinterpret_cast<uint32_t *>(base + w.o_pts);
+  uint4 *slot = reinterpret_cast<uint4 *>(base + w.o_slot);
+  uint32_t *val = reinterpret_cast<uint32_t *>(base + w.o_val);
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned int un = (unsigned int)n;
+  const unsigned int cap = (unsigned int)p->sms * 16u;
+  const unsigned int g_rect = std::min<unsigned int>((un + 255u) / 256u, cap);
+  const unsigned int g_pts = std::min<unsigned int>((unsigned int)(((unsigned long long)un * 4ull + 255ull) / 256ull), cap);
+  if (cudaMemsetAsync(cnt, 0, (size_t)p->H * 4, s) != cudaSuccess) return IHIST_ERR_CUDA;
+  corner_count_kernel<<<g_rect, 256, 0, s>>>(d_rects, un, p->H, p->W, cnt, p->ctrl);
+  row_offsets_kernel<<<1, 1024, 0, s>>>(cnt, p->H, off);
+  corner_scatter_kernel<<<g_rect, 256, 0, s>>>(d_rects, un, p->H, p->W, cnt, off, pts, slot);
+  for (int b0 = 0; b0 < p->B; b0 += nb) {
+    const int cur = std::min(nb, p->B - b0);
+    const unsigned int g_comb = std::min<unsigned int>(
+        (unsigned int)(((unsigned long long)un * nb + 255ull) / 256ull), cap);
+    switch (nb) {
+      case 4:
+        corner_gather_kernel<4><<<g_pts, 256, 0, s>>>(d_hist, p->H, p->W, b0, cur, pts, off, val);
+        corner_combine_kernel<4><<<g_comb, 256, 0, s>>>(slot, un, p->B, b0, cur, val, d_hist_out);
+        break;
+      case 8:
+        corner_gather_kernel<8><<<g_pts, 256, 0, s>>>(d_hist, p->H, p->W, b0, cur, pts, off, val);
+        corner_combine_kernel<8><<<g_comb, 256, 0, s>>>(slot, un, p->B, b0, cur, val, d_hist_out);
+        break;
+      default:
+        corner_gather_kernel<16><<<g_pts, 256, 0, s>>>(d_hist, p->H, p->W, b0, cur, pts, off, val);
+        corner_combine_kernel<16><<<g_comb, 256, 0, s>>>(slot, un, p->B, b0, cur, val, d_hist_out);
+        break;
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? IHIST_OK : IHIST_ERR_CUDA;
 }
 
 extern "C" int ihist_window_search(ihist_plan_t p, const uint32_t *d_hist, const uint32_t *d_target, int win_h,

@@ -35,28 +35,36 @@ namespace {
 constexpr int kBatchWarps = 16;  // default warps per CTA of the batched kernel
 
 // Tiling of one frame in a batched launch of `warps`-warp CTAs: m chunks
-// per warp (at most max_m) and gpc bin groups per CTA, nchunks * gpc at most
-// max_ncg (the per-CTA carry width the launch's shared memory was sized
-// for), maximising the share of the CTA's warps x m chunk slots that hold
-// columns, smaller m on ties.  Returns false if no tiling fits (the frame
-// is wider than warps x max_m chunks, or its chunks exceed max_ncg).
+// per warp (at most max_m) and gpc bin groups per CTA, chunks per CTA group
+// x gpc at most max_ncg (the per-CTA carry width the launch's shared memory
+// was sized for), maximising the share of the CTA's warps x m chunk slots
+// that hold columns, smaller m on ties.  A frame wider than warps x max_m
+// chunks is split into width segments of equal chunk counts (one work item
+// each, see the scan kernel); segments are used only when no tiling without
+// them exists.  Returns false if no tiling fits max_ncg.
 bool batch_frame_tiling(int h, int w, int nbins, int layout, int G, int R_req, int max_m, int max_ncg,
                         int warps, FrameDesc *f) {
   const int nchunks = (w + kChunk - 1) / kChunk;
   const int ngroups = (nbins + G - 1) / G;
   double best = -1.0;
-  int bm = 1, bwpg = nchunks, bgpc = 1;
-  for (int m = 1; m <= max_m; m <<= 1) {
-    const int wpg = (nchunks + m - 1) / m;
-    if (wpg > warps) continue;
-    const int gpc = std::min(std::min(ngroups, warps / wpg), max_ncg / nchunks);
-    if (gpc < 1) continue;
-    const double util = (double)nchunks * gpc / ((double)warps * m);
-    if (util > best + 1e-9) {
-      best = util;
-      bm = m;
-      bwpg = wpg;
-      bgpc = gpc;
+  int bm = 1, bwpg = nchunks, bgpc = 1, bsegs = 1;
+  for (int pass = 0; pass < 2 && best < 0.0; ++pass) {
+    for (int m = 1; m <= max_m; m <<= 1) {
+      const int wpg_all = (nchunks + m - 1) / m;
+      const int nsegs = pass == 0 ? 1 : (wpg_all + warps - 1) / warps;
+      const int wpg = (wpg_all + nsegs - 1) / nsegs;
+      if (wpg > warps) continue;
+      const int ncl = std::min(nchunks, wpg * m);
+      const int gpc = std::min(std::min(ngroups, warps / wpg), max_ncg / ncl);
+      if (gpc < 1) continue;
+      const double util = (double)nchunks * gpc / ((double)nsegs * warps * m);
+      if (util > best + 1e-9) {
+        best = util;
+        bm = m;
+        bwpg = wpg;
+        bgpc = gpc;
+        bsegs = nsegs;
+      }
     }
   }
   std::memset(f, 0, sizeof(*f));
@@ -72,11 +80,20 @@ bool batch_frame_tiling(int h, int w, int nbins, int layout, int G, int R_req, i
   f->m = bm;
   f->wpg = bwpg;
   f->gpc = bgpc;
+  f->nsegs = bsegs;
+  f->cps = bsegs > 1 ? bwpg * bm : nchunks;
   f->ngsets = (ngroups + bgpc - 1) / bgpc;
-  f->nitems = (unsigned int)f->nbands * (unsigned int)f->ngsets;
+  f->nitems = (unsigned int)f->nbands * (unsigned int)f->ngsets * (unsigned int)bsegs;
   f->fault_skip_band = -1;
   return best >= 0.0;
 }
+
+// Chunks of one CTA's bin group (the shared-memory carry width per group).
+int frame_ncl(const FrameDesc &f) { return std::min(f.nchunks, f.cps); }
+
+// Segment records of a segmented frame (0 otherwise) and their words.
+size_t frame_nhs(const FrameDesc &f) { return f.nsegs > 1 ? (size_t)f.nbands * f.ngroups * f.nsegs : 0; }
+size_t frame_hagg_words(const FrameDesc &f, int G) { return frame_nhs(f) * ((size_t)f.R * G + G); }
 
 size_t frame_nci(const FrameDesc &f) { return (size_t)f.nbands * f.ngroups * f.nchunks; }
 
@@ -155,7 +172,8 @@ struct ihist_batch_s {
   unsigned int *d_end, *d_bins_end;
   uint32_t *d_lut;                                    // table batches: [slot][256]
   std::vector<size_t> slot_nci;                       // carry capacity of each slot
-  std::vector<uint32_t *> slot_flags, slot_cnt, slot_left, slot_incl;
+  std::vector<size_t> slot_nhs, slot_hwords;          // width-segment records and their words per slot
+  std::vector<uint32_t *> slot_flags, slot_cnt, slot_left, slot_incl, slot_hflags, slot_hagg;
   std::vector<size_t> slot_idx_cap;                   // joint-bin plane bytes of each slot
   std::vector<uint8_t *> slot_idx;
   std::vector<FrameDesc> fd;                          // current frames
@@ -204,8 +222,8 @@ static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames, int n) {
     FrameDesc &f = fd[i];
     if (!batch_frame_tiling(fr.h, fr.w, fr.nbins, fr.layout, b->G, b->R_req, b->mmax, b->ncg_max, b->warps,
                             &f) ||
-        frame_nci(f) > b->slot_nci[i] || f.R > b->R_max || f.nchunks * f.gpc > b->ncg_max ||
-        mmax_for(f.m) > b->mmax)
+        frame_nci(f) > b->slot_nci[i] || f.R > b->R_max || frame_ncl(f) * f.gpc > b->ncg_max ||
+        mmax_for(f.m) > b->mmax || frame_nhs(f) > b->slot_nhs[i] || frame_hagg_words(f, b->G) > b->slot_hwords[i])
       return IHIST_ERR_UNSUPPORTED;  // does not fit the slot planned for it
     f.in = frame_joint(fr) ? b->slot_idx[i] : fr.d_in;
     f.pitch = frame_joint(fr) ? (long long)idx_pitch_of(fr.w) : (long long)fr.in_pitch;
@@ -215,6 +233,8 @@ static int batch_bind(ihist_batch_s *b, const ihist_frame_t *frames, int n) {
     f.agg_cnt = b->slot_cnt[i];
     f.agg_left = b->slot_left[i];
     f.incl = b->slot_incl[i];
+    f.hflags = frame_nhs(f) ? b->slot_hflags[i] : nullptr;
+    f.hagg = frame_nhs(f) ? b->slot_hagg[i] : nullptr;
     f.fault_skip_band = b->fault_skip_band;
     tma = tma && frame_tma_ok(fr);
     vec = vec && frame_vec_ok(fr);
@@ -408,7 +428,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
         batch_frame_tiling(frames[i].h, frames[i].w, frames[i].nbins, frames[i].layout, b->G, r, max_m, INT_MAX,
                            b->warps, &f);
         rmax = std::max(rmax, f.R);
-        ncg = std::max(ncg, f.nchunks * f.gpc);
+        ncg = std::max(ncg, frame_ncl(f) * f.gpc);
         mm = std::max(mm, f.m);
       }
       int occ = 0;
@@ -438,9 +458,11 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
                        INT_MAX, b->warps, &plan_fd[i]);
     mm = std::max(mm, plan_fd[i].m);
     b->R_max = std::max(b->R_max, plan_fd[i].R);
-    b->ncg_max = std::max(b->ncg_max, plan_fd[i].nchunks * plan_fd[i].gpc);
+    b->ncg_max = std::max(b->ncg_max, frame_ncl(plan_fd[i]) * plan_fd[i].gpc);
     b->slot_nci.push_back(frame_nci(plan_fd[i]));
-    nci_total += frame_nci(plan_fd[i]);
+    b->slot_nhs.push_back(frame_nhs(plan_fd[i]));
+    b->slot_hwords.push_back(frame_hagg_words(plan_fd[i], b->G));
+    nci_total += frame_nci(plan_fd[i]) + frame_nhs(plan_fd[i]);
   }
   b->mmax = mmax_for(mm);
   b->smem_bytes = smem_layout(b->warps, b->R_max, b->G, b->ncg_max, b->stage != 0).bytes;
@@ -492,6 +514,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
     off = align_up(off + nci * kChunk * (b->G / 4) * 4, 256);
     off = align_up(off + nci * b->G * 4, 256);
     off = align_up(off + nci * b->G * kChunk * 4, 256);
+    off = align_up(off + b->slot_hwords[i] * 4, 256);
   }
   const size_t o_idx = off;  // joint-bin planes of the slots planned with joint frames
   for (int i = 0; i < n; ++i) {
@@ -526,12 +549,16 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
     const size_t nci = b->slot_nci[i];
     b->slot_flags.push_back(reinterpret_cast<uint32_t *>(base + fo));
     fo += nci * sizeof(uint32_t);
+    b->slot_hflags.push_back(reinterpret_cast<uint32_t *>(base + fo));  // segment flags, cleared with the rest
+    fo += b->slot_nhs[i] * sizeof(uint32_t);
     b->slot_cnt.push_back(reinterpret_cast<uint32_t *>(base + co));
     co = align_up(co + nci * kChunk * (b->G / 4) * 4, 256);
     b->slot_left.push_back(reinterpret_cast<uint32_t *>(base + co));
     co = align_up(co + nci * b->G * 4, 256);
     b->slot_incl.push_back(reinterpret_cast<uint32_t *>(base + co));
     co = align_up(co + nci * b->G * kChunk * 4, 256);
+    b->slot_hagg.push_back(reinterpret_cast<uint32_t *>(base + co));
+    co = align_up(co + b->slot_hwords[i] * 4, 256);
   }
   size_t xo = o_idx;
   for (int i = 0; i < n; ++i) {

@@ -21,15 +21,22 @@
 //     above until it meets a published inclusive prefix row.
 //   * a5 store: each output word is written once, 128-bit streaming stores.
 //
-// Work item = (band k of R rows, bin group g of G bins).  The CTA's warps
-// split the frame width: warp w owns 128-column chunks [w*m, w*m + m).  Each
+// Work item = (band k of R rows, bin group g of G bins, width segment s).
+// The CTA's warps split the segment: warp w owns 128-column chunks
+// [s*cps + w*m, s*cps + w*m + m) (cps = chunks per segment; one segment
+// spans the whole width unless the frame is wider than a CTA's warps can
+// cover).  Each
 // warp stages its chunk's R x 128-byte input tile in shared memory (a TMA
 // tensor copy when the frame is 16-byte aligned, else plain loads) and reads
 // it once to count and once to emit.  The horizontal carry between warps
 // comes from the counting pass (per-row bin totals of each warp's columns,
 // one redux.sync per 4 bins) and an exclusive scan over warps in shared
-// memory.  The vertical carry between bands is the look-back, per (band,
-// group, chunk).
+// memory.  Between width segments of a band, each segment publishes its
+// per-row bin totals right after counting (they depend on its own pixels
+// only) and a segment adds those of every segment to its left: no chain, so
+// the horizontal carry costs one wait for data that is already published
+// when the segments run side by side.  The vertical carry between bands is
+// the look-back, per (band, group, chunk).
 #pragma once
 
 #include <cuda.h>
@@ -61,6 +68,11 @@ struct FrameDesc {
   uint32_t *agg_left;   // [ci][G]: band count left of the chunk
   uint32_t *incl;       // [ci][G][128]: H on the band's last row
   uint32_t *flags;      // [ci]
+  int nsegs;            // width segments per band (1: one CTA spans the width)
+  int cps;              // chunks per segment (wpg * m)
+  uint32_t *hagg;       // [(k * ngroups + g) * nsegs + s][R * G + G]: a segment's per-row bin
+                        // totals, then its band totals per bin (nsegs > 1 only)
+  uint32_t *hflags;     // [(k * ngroups + g) * nsegs + s] (nsegs > 1 only)
 };
 
 // Dynamic shared memory of one CTA, carved from a 128-byte aligned base.
@@ -238,10 +250,15 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
   constexpr int GQ = G / 4;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  const int k = (int)(it / (unsigned)f.ngsets);
-  const int gs = (int)(it % (unsigned)f.ngsets);
+  const int nsegs = f.nsegs > 1 ? f.nsegs : 1;
+  const int seg = (int)(it % (unsigned)nsegs);
+  const unsigned int kg = it / (unsigned)nsegs;
+  const int k = (int)(kg / (unsigned)f.ngsets);
+  const int gs = (int)(kg % (unsigned)f.ngsets);
   // checked builds: the item must lie inside the frame (uniform over the CTA)
   if (!IHIST_GUARD(ctrl, k < f.nbands && gs < f.ngsets)) return;
+  const int cseg0 = nsegs > 1 ? seg * f.cps : 0;                        // first chunk of the segment
+  const int nchs = nsegs > 1 ? min(f.cps, f.nchunks - cseg0) : f.nchunks;  // chunks of the segment
   const int lg = w / f.wpg;  // local bin group of this warp
   const int wg = w % f.wpg;  // warp slot within the group
   const int g = gs * f.gpc + lg;
@@ -250,15 +267,16 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
   const int nrows = min(f.R, f.H - y0);
   const Binner<LUT> bin{(uint32_t)f.qmul, s_lut};
   const uint32_t gbase = 8u * (uint32_t)(g * G);
-  const int c_begin = wg * f.m;
-  const int my_m = gvalid ? max(0, min(f.m, f.nchunks - c_begin)) : 0;  // warp-uniform
+  const int c_begin = cseg0 + wg * f.m;
+  const int my_m = gvalid ? max(0, min(f.m, cseg0 + nchs - c_begin)) : 0;  // warp-uniform
   const bool publish = (k != f.fault_skip_band);
   const unsigned int ci0 = ((unsigned)k * f.ngroups + g) * (unsigned)f.nchunks;  // chunk 0
   const unsigned int nci = (unsigned)f.nbands * f.ngroups * f.nchunks;  // carry slots of the frame
   const uint32_t *out_end = f.out + (size_t)f.H * f.W * f.B;           // end of the frame's H
   (void)nci;
   (void)out_end;
-  uint32_t *my_ctot = s_ctot + (size_t)(gvalid ? lg : 0) * f.nchunks * G;
+  // band totals per chunk of the segment, indexed by chunk - cseg0
+  uint32_t *my_ctot = s_ctot + (size_t)(gvalid ? lg : 0) * nchs * G - (size_t)cseg0 * G;
   uint8_t *tile = s_tiles + (size_t)w * f.R * kChunk;
   uint64_t *bar = s_bar + w;
   uint32_t *myrow = s_row + (size_t)w * f.R * G;
@@ -359,6 +377,10 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
   // ---- horizontal carries: exclusive scans over the warps of each bin
   // group (row carries) and over chunks (band counts left of each chunk) ----
   const int ngl = min(f.gpc, f.ngroups - gs * f.gpc);  // bin groups in this item
+  // a segment's own totals, for the segments to its right
+  const bool seg_pub = nsegs > 1 && seg < nsegs - 1 && publish;
+  const size_t hstride = (size_t)f.R * G + G;                       // words per segment record
+  const unsigned int hbase = ((unsigned)k * f.ngroups + gs * f.gpc) * (unsigned)nsegs;  // group lg: + lg * nsegs
   for (int e = threadIdx.x; e < ngl * nrows * G; e += blockDim.x) {
     const int l = e / (nrows * G), r = e - l * (nrows * G);
     uint32_t run = 0u;
@@ -368,15 +390,47 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
       *p = run;
       run += v;
     }
+    if (seg_pub) f.hagg[(size_t)(hbase + l * nsegs + seg) * hstride + r] = run;
   }
   for (int e = threadIdx.x; e < ngl * G; e += blockDim.x) {
     const int l = e / G, b = e - l * G;
     uint32_t run = 0u;
-    for (int c = 0; c < f.nchunks; ++c) {
-      uint32_t *p = s_ctot + ((size_t)l * f.nchunks + c) * G + b;
+    for (int c = 0; c < nchs; ++c) {
+      uint32_t *p = s_ctot + ((size_t)l * nchs + c) * G + b;
       const uint32_t v = *p;
       *p = run;
       run += v;
+    }
+    if (seg_pub) f.hagg[(size_t)(hbase + l * nsegs + seg) * hstride + (size_t)f.R * G + b] = run;
+  }
+  if (nsegs > 1) {
+    // publish this segment's totals (poisoned if any warp's staging failed),
+    // then add the totals of every segment to the left
+    if (seg_pub) __threadfence();
+    const bool bad = __syncthreads_or(!stage_ok);
+    if (seg_pub && threadIdx.x < ngl)
+      st_release_gpu(f.hflags + hbase + threadIdx.x * nsegs + seg, (epoch << 2) | (bad ? kStatePoison : kStateAgg));
+    bool hpoison = bad;
+    for (int l = 0; l < ngl && !hpoison; ++l)
+      for (int j = 0; j < seg && !hpoison; ++j)
+        if (wait_flag(f.hflags + hbase + l * nsegs + j, epoch, ctrl, timeout_ns) == kStatePoison) hpoison = true;
+    hpoison = __syncthreads_or(hpoison);
+    if (hpoison) {
+      stage_ok = false;  // publish poison below and emit nothing
+    } else if (seg > 0) {
+      for (int e = threadIdx.x; e < ngl * nrows * G; e += blockDim.x) {
+        const int l = e / (nrows * G), r = e - l * (nrows * G);
+        uint32_t left = 0u;
+        for (int j = 0; j < seg; ++j) left += ld_relaxed_u32(f.hagg + (size_t)(hbase + l * nsegs + j) * hstride + r);
+        for (int ww = 0; ww < f.wpg; ++ww) s_row[(size_t)(l * f.wpg + ww) * f.R * G + r] += left;
+      }
+      for (int e = threadIdx.x; e < ngl * G; e += blockDim.x) {
+        const int l = e / G, b = e - l * G;
+        uint32_t left = 0u;
+        for (int j = 0; j < seg; ++j)
+          left += ld_relaxed_u32(f.hagg + (size_t)(hbase + l * nsegs + j) * hstride + (size_t)f.R * G + b);
+        for (int c = 0; c < nchs; ++c) s_ctot[((size_t)l * nchs + c) * G + b] += left;
+      }
     }
   }
   __syncthreads();
@@ -669,7 +723,8 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
   __shared__ uint32_t s_lut[LUT ? 256 : 1];
   const int NW = blockDim.x >> 5;
   const bool stage = pm_staged(f.layout, G);
-  const SmemLayout L = smem_layout(NW, f.R, G, f.nchunks * f.gpc, stage);
+  const int ncl = f.nsegs > 1 ? min(f.nchunks, f.cps) : f.nchunks;  // chunks of one CTA group
+  const SmemLayout L = smem_layout(NW, f.R, G, ncl * f.gpc, stage);
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   uint4 *s_stage = stage ? reinterpret_cast<uint4 *>(base + L.stage_off) : nullptr;

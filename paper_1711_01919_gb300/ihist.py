@@ -40,7 +40,7 @@ EXPORTED = (
     "ihist_batch_items", "ihist_batch_destroy", "ihist_batch_query_all", "ihist_batch_upload_compute",
     "ihist_compute_noalloc", "ihist_plan_lut", "ihist_plan_edges", "ihist_plan_joint",
     "ihist_plan_channels", "ihist_window_search", "ihist_mapping_workspace_bytes", "ihist_mapping_compute",
-    "ihist_batch_get_tune", "ihist_edges_table",
+    "ihist_batch_get_tune", "ihist_edges_table", "ihist_query_work_bytes", "ihist_query_sorted",
 )
 
 
@@ -112,6 +112,10 @@ def load(path: str = LIB_PATH):
         L.ihist_compute.restype = ci
         L.ihist_query.argtypes = [vp, vp, vp, ci, vp, vp]
         L.ihist_query.restype = ci
+        L.ihist_query_work_bytes.argtypes = [vp, ci, ci]
+        L.ihist_query_work_bytes.restype = sz
+        L.ihist_query_sorted.argtypes = [vp, vp, vp, ci, vp, ci, vp, sz, vp]
+        L.ihist_query_sorted.restype = ci
         L.ihist_sequence_host.argtypes = [vp, vp, sz, ci, vp, vp, ci, vp, ci, vp, vp, vp, vp]
         L.ihist_sequence_host.restype = ci
         L.ihist_status.argtypes = [vp, vp, ctypes.POINTER(ci)]
@@ -261,6 +265,16 @@ def ihist_compute(plan: int, d_in: int, in_pitch: int, d_out: int, stream: int =
 
 def ihist_query(plan: int, d_hist: int, d_rects: int, n: int, d_hist_out: int, stream: int = 0) -> None:
     _check(load().ihist_query(plan, d_hist, d_rects, n, d_hist_out, stream), "ihist_query")
+
+
+def ihist_query_work_bytes(plan: int, n: int, bins_per_pass: int = 0) -> int:
+    return int(load().ihist_query_work_bytes(plan, n, bins_per_pass))
+
+
+def ihist_query_sorted(plan: int, d_hist: int, d_rects: int, n: int, d_hist_out: int, bins_per_pass: int,
+                       d_work: int, work_bytes: int, stream: int = 0) -> None:
+    _check(load().ihist_query_sorted(plan, d_hist, d_rects, n, d_hist_out, bins_per_pass, d_work, work_bytes,
+                                     stream), "ihist_query_sorted")
 
 
 def ihist_window_search(plan: int, d_hist: int, d_target: int, win_h: int, win_w: int, stride: int,
@@ -503,6 +517,28 @@ class Plan:
             out = torch.empty((n, self.nbins), dtype=torch.int32, device=rects.device)
         ihist_query(self.handle, hist.data_ptr(), rects.data_ptr(), n, out.data_ptr(), _stream(stream))
         return out
+
+    def query_sorted(self, hist, rects, out=None, work=None, bins_per_pass: int = 0, stream=None):
+        """As query, with the corners bucketed by row first (bin-major plans,
+        large batches; see ihist_query_sorted).  work: a CUDA uint8 scratch
+        tensor of query_work_bytes(n) bytes (allocated here if None)."""
+        import torch
+        if rects.dtype != torch.int32 or not rects.is_contiguous() or rects.dim() != 2 or rects.shape[1] != 4:
+            raise ValueError("rects must be a contiguous int32 [n][4] tensor")
+        n = rects.shape[0]
+        if out is None:
+            out = torch.empty((n, self.nbins), dtype=torch.int32, device=rects.device)
+        need = self.query_work_bytes(n, bins_per_pass)
+        if work is None:
+            work = torch.empty((need,), dtype=torch.uint8, device=rects.device)
+        if work.numel() < need or work.data_ptr() % 256:
+            raise ValueError("work must be a 256-byte aligned uint8 tensor of %d bytes" % need)
+        ihist_query_sorted(self.handle, hist.data_ptr(), rects.data_ptr(), n, out.data_ptr(), bins_per_pass,
+                           work.data_ptr(), work.numel(), _stream(stream))
+        return out
+
+    def query_work_bytes(self, n: int, bins_per_pass: int = 0) -> int:
+        return ihist_query_work_bytes(self.handle, n, bins_per_pass)
 
     def window_search(self, hist, target, win_h: int, win_w: int, stride: int, out=None, stream=None):
         """Histogram-intersection score of every win_h x win_w window on a

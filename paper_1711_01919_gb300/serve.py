@@ -95,20 +95,17 @@ class Done:
     status: str = "ok"        # ok | rejected
     target: int = -1
     t_launch: float = -1.0    # host time of the launch that served it
+    launch_n: int = 0         # frames: how many frames shared that launch (1 = a per-frame launch)
 
 
 def hist_bytes(h: int, w: int, nbins: int) -> int:
     return h * w * nbins * 4
 
 
-# Widest frame a batched launch takes (16-warp CTAs, 4 chunks of 128 columns each).
-MAX_BATCH_WIDTH = 8192
-
-
 def frame_supported(h: int, w: int, nbins: int) -> bool:
     """Shapes both executors take: the library's frame limits (1 <= h, w <=
-    65535, h * w < 2^32, 1 <= nbins <= 256) and the batched launch's width."""
-    return 1 <= h <= 65535 and 1 <= w <= MAX_BATCH_WIDTH and h * w < (1 << 32) and 1 <= nbins <= 256
+    65535, h * w < 2^32, 1 <= nbins <= 256)."""
+    return 1 <= h <= 65535 and 1 <= w <= 65535 and h * w < (1 << 32) and 1 <= nbins <= 256
 
 
 class HistStore:
@@ -315,7 +312,8 @@ class Server:
                         for r in obj:
                             self.store.set_ready(r.rid, h["payloads"][r.rid])
                             self.store.touch(r.rid)
-                            self.done.append(Done(r.rid, "frame", r.t_arrival, td, t_launch=h["t_launch"]))
+                            self.done.append(Done(r.rid, "frame", r.t_arrival, td, t_launch=h["t_launch"],
+                                                  launch_n=len(obj)))
                     else:
                         self.store.unpin(obj.target)
                         self.store.touch(obj.target)
@@ -347,6 +345,19 @@ class Server:
                 "launch_wait_p99_ms": float(np.percentile(wait, 99)) if len(wait) else None,
                 "per_s": len(ok) / wall_s if wall_s > 0 else None,
             }
+        # frame latency by the path that served it: per-frame launches and
+        # shared (batched) launches
+        frames = [d for d in self.done if d.kind == "frame" and d.status == "ok"]
+        by_path = {}
+        for name, sel in (("solo", [d for d in frames if d.launch_n == 1]),
+                          ("shared", [d for d in frames if d.launch_n > 1])):
+            lat = np.array([d.t_done - d.t_arrival for d in sel]) * 1e3
+            wait = np.array([d.t_launch - d.t_arrival for d in sel]) * 1e3
+            by_path[name] = {"frames": len(sel),
+                             "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                             "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                             "launch_wait_p99_ms": float(np.percentile(wait, 99)) if len(wait) else None}
+        out["frame"]["by_path"] = by_path
         return out
 
 

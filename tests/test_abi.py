@@ -56,9 +56,10 @@ def test_plan_rejects_bad_tuning(lib):
         with pytest.raises(ihist.IhistError) as e:
             ihist.ihist_plan_tuned(16, 16, 4, 0, tune)
         assert e.value.code == ihist.IHIST_ERR_INVALID_ARG
-    with pytest.raises(ihist.IhistError) as e:
-        ihist.ihist_plan(16, 20000, 4, 0)
-    assert e.value.code == ihist.IHIST_ERR_UNSUPPORTED
+    for h, w in ((16, 65536), (65536, 16), (0, 16), (16, 0)):  # outside 1 <= h, w <= 65535
+        with pytest.raises(ihist.IhistError) as e:
+            ihist.ihist_plan(h, w, 4, 0)
+        assert e.value.code == ihist.IHIST_ERR_INVALID_ARG
 
 
 def test_null_plan_calls_are_rejected(lib):

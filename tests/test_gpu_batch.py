@@ -209,8 +209,7 @@ def test_set_io_narrower_frames_keep_the_planned_launch_shape():
             check_batch(batch, imgs, [b for (h, w, b) in shapes], [0, 0])
 
 
-def test_warps_per_cta_4_and_too_wide_frames_are_rejected():
-    # 4-warp CTAs: 300x4096 needs 32 chunks = 8 per warp > 4, so the plan is refused
+def test_warps_per_cta_4_and_wide_frames_in_width_segments():
     small = [(37, 131, 16, 0), (240, 320, 16, 0), (64, 257, 7, 1), (100, 1000, 64, 1)]
     imgs = [synth.uniform_frame(2000 + i, h, w) for i, (h, w, b, l) in enumerate(small)]
     nbins = [b for (h, w, b, l) in small]
@@ -220,14 +219,24 @@ def test_warps_per_cta_4_and_too_wide_frames_are_rejected():
         batch.compute()
         assert batch.status() == ihist.IHIST_OK
         check_batch(batch, imgs, nbins, layouts)
-    wide = [torch.zeros((300, 4096), dtype=torch.uint8, device="cuda")]
-    with pytest.raises(ihist.IhistError) as e:
-        ihist.Batch(wide, [8], tune={"warps_per_cta": 4})
-    assert e.value.code == ihist.IHIST_ERR_UNSUPPORTED
-    # 16-warp CTAs reach 16 x 4 chunks = 8192 columns; wider frames are refused
-    with pytest.raises(ihist.IhistError) as e:
-        ihist.Batch([torch.zeros((16, 9000), dtype=torch.uint8, device="cuda")], [8])
-    assert e.value.code == ihist.IHIST_ERR_UNSUPPORTED
+    # frames wider than a CTA's warps x 4 chunks: each band splits into width
+    # segments (4-warp CTAs: 300x4096 needs 32 chunks = 2 segments; 16-warp
+    # CTAs: 9000 columns = 2 segments, 20000 = 3, 65535 = 8), mixed with
+    # ordinary frames in one launch
+    for shapes, tune in (([(300, 4096, 8, 0), (50, 700, 16, 1)], {"warps_per_cta": 4}),
+                         ([(16, 9000, 8, 0), (240, 320, 16, 0)], None),
+                         ([(70, 20000, 12, 0), (33, 20000, 32, 2), (480, 640, 32, 0), (5, 20000, 16, 1)], None),
+                         ([(9, 65535, 5, 0), (61, 333, 9, 0)], {"rows_per_band": 4})):
+        imgs = [synth.uniform_frame(2100 + i + w, h, w) for i, (h, w, b, l) in enumerate(shapes)]
+        nbins = [b for (h, w, b, l) in shapes]
+        layouts = [l for (h, w, b, l) in shapes]
+        with ihist.Batch([torch.from_numpy(x).cuda() for x in imgs], nbins, layouts, tune=tune) as batch:
+            batch.compute()
+            assert batch.status() == ihist.IHIST_OK
+            check_batch(batch, imgs, nbins, layouts)
+            batch.compute()  # the next launch (other epoch) is exact too
+            assert batch.status() == ihist.IHIST_OK
+            check_batch(batch, imgs, nbins, layouts)
 
 
 def test_pixel_major_batch_defaults_to_16_bin_groups():

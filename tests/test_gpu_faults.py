@@ -46,6 +46,29 @@ def test_lookback_timeout_is_bounded_and_reported(skip_band):
         assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(nbins, h, w), ref)
 
 
+@pytest.mark.parametrize("skip_band", [0, 3])
+def test_width_segment_timeout_is_bounded_and_reported(skip_band):
+    # 3000 columns at one chunk per warp: each band is two width segments; the
+    # band whose CTAs publish nothing leaves its right segment (and the band
+    # below) waiting, both waits run out, and the next launch is exact
+    h, w, nbins = 32, 3000, 8
+    img = synth.uniform_frame(3, h, w)
+    tune = {"rows_per_band": 8, "chunks_per_warp": 1, "fault_skip_band": skip_band + 1, "timeout_us": 20000}
+    ref = oracle.integral_histogram(img, nbins)
+    with ihist.Plan(h, w, nbins, 0, tune=tune) as plan:
+        d_img = torch.from_numpy(img).cuda()
+        t0 = time.time()
+        plan.compute(d_img)
+        st = plan.status()
+        assert time.time() - t0 < 5.0
+        assert st == ihist.IHIST_ERR_LOOKBACK_TIMEOUT
+    with ihist.Plan(h, w, nbins, 0, tune={"rows_per_band": 8, "chunks_per_warp": 1}) as plan:
+        for _ in range(2):
+            out = plan.compute(torch.from_numpy(img).cuda())
+            assert plan.status() == ihist.IHIST_OK
+            assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(nbins, h, w), ref)
+
+
 def test_plan_recovers_after_timeout_launch():
     # a plan whose previous launch timed out runs the next launch cleanly
     # (flags carry the launch epoch, so stale ones are ignored)

@@ -49,7 +49,7 @@ def big():
     d_rects = torch.from_numpy(rects).cuda()
     q = plan.query(out, d_rects)
     st = plan.status()
-    yield img, rects, d_img, out, d_rects, q, st
+    yield img, rects, d_img, out, d_rects, q, st, plan
     del out, q
     plan.close()
     torch.cuda.empty_cache()
@@ -61,7 +61,7 @@ def test_status_ok(big):
 
 @pytest.mark.parametrize("k", SAMPLE_PLANES)
 def test_sampled_plane_vs_oracle(big, k):
-    img, _, _, out, _, _, _ = big
+    img, _, _, out, _, _, _, _ = big
     ref = oracle.integral_histogram_plane(img, NBINS, k)
     got = out[k].cpu().numpy().view(np.uint32)
     assert np.array_equal(got, ref), "plane %d: %d words differ" % (k, int((got != ref).sum()))
@@ -90,7 +90,7 @@ def oracle_digests(big):
 def test_every_plane_vs_oracle_by_digest(big, oracle_digests):
     # all 128 planes (32 GiB): the GPU planes are copied back and hashed in
     # threads; equal SHA-256 digests per plane mean equal words.
-    img, _, _, out, _, _, _ = big
+    img, _, _, out, _, _, _, _ = big
 
     def gpu_digest(k):
         return k, hashlib.sha256(out[k].cpu().numpy()).hexdigest()
@@ -106,7 +106,7 @@ def test_every_plane_vs_oracle_by_digest(big, oracle_digests):
 
 
 def test_every_word_by_second_difference(big):
-    _, _, d_img, out, _, _, _ = big
+    _, _, d_img, out, _, _, _, _ = big
     binned = (d_img.to(torch.int32) * NBINS) >> 8
     for b0 in range(0, NBINS, 8):
         P = out[b0:b0 + 8]
@@ -120,7 +120,7 @@ def test_every_word_by_second_difference(big):
 
 
 def test_bottom_row_and_right_column_sums(big):
-    img, _, _, out, _, _, _ = big
+    img, _, _, out, _, _, _, _ = big
     bottom = out[:, H - 1, :].to(torch.int64).sum(0).cpu().numpy()
     right = out[:, :, W - 1].to(torch.int64).sum(0).cpu().numpy()
     assert np.array_equal(bottom, H * np.arange(1, W + 1))
@@ -130,7 +130,7 @@ def test_bottom_row_and_right_column_sums(big):
 
 
 def test_queries(big):
-    img, rects, _, out, d_rects, q, _ = big
+    img, rects, _, out, d_rects, q, _, _ = big
     area = ((d_rects[:, 2] - d_rects[:, 0] + 1).to(torch.int64) * (d_rects[:, 3] - d_rects[:, 1] + 1))
     assert torch.equal(q.to(torch.int64).sum(1), area)
     for k in SAMPLE_PLANES:  # 64, 101 and 127 read H past element offset 2^32
@@ -148,3 +148,14 @@ def test_queries_every_bin_vs_oracle_by_digest(big, oracle_digests):
         if hashlib.sha256(col).hexdigest() != oracle_digests[k][1]:
             bad.append(k)
     assert not bad, "query columns of %d bins differ from the oracle's Eq. 2, first bin %d" % (len(bad), bad[0])
+
+
+@pytest.mark.parametrize("bpp", [0, 16])
+def test_sorted_queries_equal_the_checked_queries(big, bpp):
+    # the row-bucketed query on the same 2^20 rectangles equals the plain
+    # query word for word (the plain one is checked against the oracle above)
+    _, _, _, out, d_rects, q, _, plan = big
+    got = plan.query_sorted(out, d_rects, bins_per_pass=bpp)
+    assert plan.status() == ihist.IHIST_OK
+    assert torch.equal(got, q)
+    del got

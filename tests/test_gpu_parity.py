@@ -241,11 +241,44 @@ def test_query_edge_rectangles_and_bad_rect_status():
 
 
 @pytest.mark.parametrize("h,w,nbins,layout", [(9, 16384, 5, 0), (9, 16384, 5, 1), (65535, 3, 2, 0), (65535, 3, 2, 1),
-                                              (40, 300, 256, 1), (3, 8192, 256, 0), (1, 16384, 1, 0)])
+                                              (40, 300, 256, 1), (3, 8192, 256, 0), (1, 16384, 1, 0),
+                                              (9, 65535, 5, 0), (9, 65535, 5, 1), (9, 65535, 8, 2),
+                                              (3, 40000, 256, 0), (3, 40000, 256, 1), (3, 40000, 256, 2),
+                                              (1, 65535, 1, 0)])
 def test_extreme_shapes(h, w, nbins, layout):
-    # the widest frame a plan takes (16384 columns), the tallest (65535 rows)
-    # and 256 bins in both layouts
+    # the widest frames (65535 columns: width segments), the tallest (65535
+    # rows) and 256 bins in every layout
     img = synth.uniform_frame(h + 3 * w + nbins, h, w)
     got = run_gpu(img, nbins, layout=layout)
     assert_same(got, to_layout(oracle.integral_histogram(img, nbins), layout),
                 "%dx%d B=%d layout %d" % (h, w, nbins, layout))
+
+
+@pytest.mark.parametrize("h,w,nbins,layout,tune", [
+    # one chunk per warp: 24-chunk frames split into 2 segments of 12 warps
+    (100, 3000, 16, 0, {"chunks_per_warp": 1}), (100, 3000, 16, 1, {"chunks_per_warp": 1}),
+    (100, 3000, 16, 2, {"chunks_per_warp": 1}),
+    (97, 5000, 37, 0, {"chunks_per_warp": 1, "rows_per_band": 5}),           # 3 segments, ragged tail
+    (64, 4100, 64, 1, {"chunks_per_warp": 2, "bins_per_cta": 16}),           # 17 warps -> 2 segments
+    (130, 20000, 24, 0, {"bins_per_cta": 8, "rows_per_band": 17}), (130, 20000, 24, 1, None),
+    (300, 17000, 4, 0, {"chunks_per_warp": 8, "ctas_per_sm": 1}),            # 133 chunks -> 2 segments
+    (2, 65535, 64, 0, None), (255, 33000, 16, 2, {"rows_per_band": 64}),
+])
+def test_width_segments(h, w, nbins, layout, tune):
+    # frames wider than one CTA's warps cover: each band's segments add the
+    # per-row bin totals of the segments to their left (Eq. 1's row sums
+    # split at the segment edges); exact against Algorithm 1 word for word
+    img = synth.uniform_frame(h * 7 + w + nbins, h, w)
+    got = run_gpu(img, nbins, layout=layout, tune=tune)
+    assert_same(got, to_layout(oracle.integral_histogram(img, nbins), layout),
+                "%dx%d B=%d layout %d %s" % (h, w, nbins, layout, tune))
+
+
+def test_width_segments_pitched_and_gradient():
+    # a pitched, unaligned wide input (plain loads, no TMA) and a smooth frame
+    # whose bins change slowly across the segment edges
+    h, w, nbins = 40, 30000, 32
+    img = synth.gradient_frame(77, h, w)
+    ref = oracle.integral_histogram(img, nbins)
+    assert_same(run_gpu(img, nbins, pitch_pad=13, offset=1), ref, "pitched wide frame")
+    assert_same(run_gpu(img, nbins, tune={"chunks_per_warp": 1, "rows_per_band": 3}), ref, "1 chunk per warp")

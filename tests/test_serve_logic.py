@@ -53,15 +53,17 @@ def test_oversized_frame_rejected():
 
 
 def test_unsupported_shapes_are_rejected_not_launched():
-    reqs = [serve.FrameRequest(0, 0.0, 10, 10, 4), serve.FrameRequest(1, 0.0, 10, 20000, 4),
+    reqs = [serve.FrameRequest(0, 0.0, 10, 10, 4), serve.FrameRequest(1, 0.0, 10, 70000, 4),
             serve.FrameRequest(2, 0.0, 10, 10, 300), serve.FrameRequest(3, 0.0, 0, 10, 4),
-            serve.FrameRequest(4, 0.0, 10, 10, 0), serve.FrameRequest(5, 0.0, 10, 8192, 4)]
+            serve.FrameRequest(4, 0.0, 10, 10, 0), serve.FrameRequest(5, 0.0, 10, 8192, 4),
+            serve.FrameRequest(6, 0.0, 3, 20000, 4), serve.FrameRequest(7, 0.0, 70000, 10, 4)]
     ex = serve.FakeExecutor()
     srv = serve.Server(ex, budget_bytes=1 << 30)
     done = {d.rid: d.status for d in srv.run(reqs, Clock())}
-    assert done == {0: "ok", 1: "rejected", 2: "rejected", 3: "rejected", 4: "rejected", 5: "ok"}
+    assert done == {0: "ok", 1: "rejected", 2: "rejected", 3: "rejected", 4: "rejected", 5: "ok", 6: "ok",
+                    7: "rejected"}
     launched = [rid for l in ex.launches if l[0] == "frames" for rid in l[1]]
-    assert sorted(launched) == [0, 5]
+    assert sorted(launched) == [0, 5, 6]
 
 
 def test_query_pins_its_target_until_answered():
