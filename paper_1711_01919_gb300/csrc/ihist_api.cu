@@ -253,10 +253,12 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
     if (t.bins_per_cta == 16) t.chunks_per_warp = std::min(t.chunks_per_warp, 2);  // the 16-bin kernels' limit
   }
   if (t.timeout_us == 0) t.timeout_us = kDefaultTimeoutUs;
-  // Frames wider than 16 warps x m chunks split each band into width
-  // segments of equal chunk counts, one work item each (see the scan kernel).
+  // Frames wider than 16 warps x m chunks (16 / groups_per_cta warps when
+  // that is given) split each band into width segments of equal chunk
+  // counts, one work item each (see the scan kernel).
   const int wpg_all = (nchunks + t.chunks_per_warp - 1) / t.chunks_per_warp;
-  const int nsegs = (wpg_all + 15) / 16;
+  const int seg_warps = 16 / std::max(1, t.groups_per_cta);  // warps of one group, 16 per CTA in all
+  const int nsegs = (wpg_all + seg_warps - 1) / seg_warps;
   const int wpg = (wpg_all + nsegs - 1) / nsegs;
   const int cps = wpg * t.chunks_per_warp;
   const int ncl = std::min(nchunks, cps);  // chunks of one CTA's group

@@ -46,7 +46,9 @@ MIXED = [(1, 1, 1, 0), (5, 3, 3, 1), (37, 131, 16, 0), (240, 320, 16, 0), (64, 2
 @pytest.mark.parametrize("tune", [None, {"rows_per_band": 8}, {"rows_per_band": 64, "bins_per_cta": 8},
                                   {"rows_per_band": 3, "ctas_per_sm": 1}, {"warps_per_cta": 8},
                                   {"warps_per_cta": 8, "bins_per_cta": 8, "rows_per_band": 40},
-                                  {"bins_per_cta": 16}, {"bins_per_cta": 16, "rows_per_band": 9}])
+                                  {"bins_per_cta": 16}, {"bins_per_cta": 16, "rows_per_band": 9},
+                                  {"bins_per_cta": 8, "warps_per_cta": 16}, {"bins_per_cta": 8, "warps_per_cta": 8,
+                                                                             "rows_per_band": 20}])
 def test_mixed_batch(tune):
     imgs = [synth.uniform_frame(1000 + i, h, w) for i, (h, w, b, l) in enumerate(MIXED)]
     nbins = [b for (h, w, b, l) in MIXED]

@@ -282,3 +282,16 @@ def test_width_segments_pitched_and_gradient():
     ref = oracle.integral_histogram(img, nbins)
     assert_same(run_gpu(img, nbins, pitch_pad=13, offset=1), ref, "pitched wide frame")
     assert_same(run_gpu(img, nbins, tune={"chunks_per_warp": 1, "rows_per_band": 3}), ref, "1 chunk per warp")
+
+
+@pytest.mark.parametrize("h,w,nbins,tune", [
+    (30, 9000, 24, {"bins_per_cta": 8, "groups_per_cta": 2, "chunks_per_warp": 8}),  # 2 groups in 2 segments
+    (45, 5000, 36, {"groups_per_cta": 4, "chunks_per_warp": 2, "rows_per_band": 9}),  # 4 groups in 5 segments
+])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_width_segments_with_several_groups_per_cta(h, w, nbins, tune, layout):
+    # groups_per_cta > 1 leaves 16 / groups_per_cta warps to a group, so
+    # narrower frames already split into segments
+    img = synth.uniform_frame(h + 5 * w + nbins, h, w)
+    ref = to_layout(oracle.integral_histogram(img, nbins), layout)
+    assert_same(run_gpu(img, nbins, layout=layout, tune=tune), ref, "%s %dx%d B=%d" % (tune, h, w, nbins))

@@ -22,8 +22,12 @@ def _lib():
 
 
 def edge_rects(h, w):
-    return np.array([[0, 0, w - 1, h - 1], [0, 0, 0, 0], [w - 1, h - 1, w - 1, h - 1], [0, 3, 5, h - 1],
-                     [2, 0, w - 1, 1], [0, h - 1, w - 1, h - 1], [w - 1, 0, w - 1, h - 1]], dtype=np.int32)
+    """Rectangles on the frame's edges (corners at row or column -1 are
+    absent from Eq. 2); only those inside the frame are kept."""
+    r = np.array([[0, 0, w - 1, h - 1], [0, 0, 0, 0], [w - 1, h - 1, w - 1, h - 1], [0, 3, 5, h - 1],
+                  [2, 0, w - 1, 1], [0, h - 1, w - 1, h - 1], [w - 1, 0, w - 1, h - 1]], dtype=np.int32)
+    ok = (r[:, 0] <= r[:, 2]) & (r[:, 2] < w) & (r[:, 1] <= r[:, 3]) & (r[:, 3] < h)
+    return r[ok]
 
 
 @pytest.mark.parametrize("h,w,nbins,n,bpp", [(37, 131, 37, 777, 0), (37, 131, 37, 777, 4), (37, 131, 37, 777, 16),
