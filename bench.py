@@ -62,9 +62,11 @@ def parse_args():
                     help="simulated seconds of the serving workload per server mode (0 = skip)")
     ap.add_argument("--frames", type=int, default=64,
                     help="frames per step (64 = the workload; smaller only for profiler captures)")
-    ap.add_argument("--case", choices=("sequence", "mp64-slice"), default="sequence",
+    ap.add_argument("--case", choices=("sequence", "mp64-slice", "query-slice"), default="sequence",
                     help="mp64-slice: only a few launches of the 8192x8192 x 128-bin scan's launch shape "
-                         "on the top --slice-rows rows (a profiler capture of that kernel at a few GB)")
+                         "on the top --slice-rows rows (a profiler capture of that kernel at a few GB); "
+                         "query-slice: the plain and the row-bucketed region query of 2^18 rectangles on "
+                         "the top 1024 rows of that frame (4 GiB of H)")
     ap.add_argument("--slice-rows", type=int, default=768)
     return ap.parse_args()
 
@@ -333,6 +335,46 @@ def run_mp64_slice(args) -> int:
     return 0
 
 
+def run_query_slice(args) -> int:
+    """The two bin-major region queries (ihist_query, ihist_query_sorted with
+    8 bins per pass) on the top 1024 rows of the 8192x8192 x 128-bin frame,
+    2^18 random rectangles: the launches a profiler captures for the query's
+    DRAM traffic at 4 GiB of H (more than 129 MB of L2, as at full size)."""
+    import torch
+
+    from paper_1711_01919_gb300 import build as cuda_build
+    from paper_1711_01919_gb300 import ihist, synth
+    cuda_build.build()
+    ihist.load()
+    h, w, b, n = 1024, 8192, 128, 1 << 18
+    img = torch.from_numpy(synth.sinusoid_frame(synth.workload_seed(5), 8192, w)[:h].copy()).cuda()
+    rects = torch.from_numpy(synth.rects(synth.workload_seed(5) + 1, n, h, w)).cuda()
+    s = torch.cuda.current_stream().cuda_stream
+    with ihist.Plan(h, w, b) as plan:
+        out = plan.compute(img)
+        q1 = torch.empty((n, b), dtype=torch.int32, device="cuda")
+        q2 = torch.empty_like(q1)
+        work = torch.empty((plan.query_work_bytes(n, 8),), dtype=torch.uint8, device="cuda")
+        ms = {"plain": [], "sorted": []}
+        for k in range(args.warmup + args.steps):
+            for name in ("plain", "sorted"):
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                if name == "plain":
+                    ihist.ihist_query(plan.handle, out.data_ptr(), rects.data_ptr(), n, q1.data_ptr(), s)
+                else:
+                    ihist.ihist_query_sorted(plan.handle, out.data_ptr(), rects.data_ptr(), n, q2.data_ptr(), 8,
+                                             work.data_ptr(), work.numel(), s)
+                e.record()
+                torch.cuda.synchronize()
+                if k >= args.warmup:
+                    ms[name].append(a.elapsed_time(e))
+        if plan.status() != ihist.IHIST_OK or not torch.equal(q1, q2):
+            raise SystemExit("query slice: device status error or the two queries differ")
+        print(json.dumps({"case": "query-slice", "rows": h, "W": w, "B": b, "rects": n, "ms": ms}), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -380,6 +422,11 @@ def serving_report(seconds: float) -> dict:
     out = {"workload": "Poisson arrivals for %.1f s: frames at 2000/s (320x240..1920x1080, 16-64 bins), "
                        "queries of 10,000 rects at 200/s and searches for a 64x64 patch (stride 8) at 50/s "
                        "against a random resident histogram; 40 GB budget, LRU eviction" % seconds}
+    # a short discarded pass of each server first: the first seconds of a
+    # process's first serving runs measured slower whichever server ran first
+    # (frame p99 0.52-0.55 ms against 0.43 ms once both had run)
+    for mode in ("batched", "plain"):
+        serve.serve(mode=mode, duration_s=min(seconds, 2.0))
     for mode in ("batched", "plain"):
         rep = serve.serve(mode=mode, duration_s=seconds)
         out[mode] = {k: {f: rep[k][f] for f in keep} for k in ("frame", "query", "search")}
@@ -757,6 +804,8 @@ def main():
         return run_reference(args)
     if args.case == "mp64-slice":
         return run_mp64_slice(args)
+    if args.case == "query-slice":
+        return run_query_slice(args)
     import torch
     import torch.distributed as dist
 

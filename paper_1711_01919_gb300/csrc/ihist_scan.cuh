@@ -599,25 +599,22 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
       // top = inclusive row found + the aggregates passed (Eq. 1 split into
       // the count left of the chunk and a prefix across the chunk)
       uint32_t acc[G][4];  // becomes the running H of this lane's 4 columns
-      if (incl_at >= 0) {
-        const unsigned int cj = ((unsigned)incl_at * f.ngroups + g) * (unsigned)f.nchunks + c;
+      // bin by bin, so each bin's aggregate sums are dead once its row is in
+      // acc (fewer registers live at once than loading the whole row first)
+      const unsigned int cji = ((unsigned)(incl_at >= 0 ? incl_at : 0) * f.ngroups + g) * (unsigned)f.nchunks + c;
 #pragma unroll
-        for (int b = 0; b < G; ++b) {
-          const uint4 v = ld_relaxed_v4(f.incl + ((size_t)cj * G + b) * kChunk + 4 * lane);
+      for (int b = 0; b < G; ++b) {
+        if (incl_at >= 0) {
+          const uint4 v = ld_relaxed_v4(f.incl + ((size_t)cji * G + b) * kChunk + 4 * lane);
           acc[b][0] = v.x;
           acc[b][1] = v.y;
           acc[b][2] = v.z;
           acc[b][3] = v.w;
-        }
-      } else {
-#pragma unroll
-        for (int b = 0; b < G; ++b)
+        } else {
 #pragma unroll
           for (int i = 0; i < 4; ++i) acc[b][i] = 0u;
-      }
-      if (summed) {
-#pragma unroll
-        for (int b = 0; b < G; ++b) {
+        }
+        if (summed) {
           const int q = b >> 2, h = (b >> 1) & 1, sh = (b & 1) * 16;
           uint32_t v[4];
 #pragma unroll
@@ -628,28 +625,26 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
         }
       }
       // inclusive row of this band = top + own aggregate, for the bands below
+      // (own column counts read one 4-bin quad at a time)
       const uint32_t *own = f.agg_cnt + ((size_t)ci * kChunk + 4 * lane) * GQ;
-      uint32_t ow[4 * GQ];
 #pragma unroll
-      for (int jj = 0; jj < GQ; ++jj) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(own + 4 * jj);
-        ow[4 * jj + 0] = v.x;
-        ow[4 * jj + 1] = v.y;
-        ow[4 * jj + 2] = v.z;
-        ow[4 * jj + 3] = v.w;
-      }
+      for (int q = 0; q < GQ; ++q) {
+        uint32_t ow[4];  // bins 4q..4q+3 of this lane's 4 columns: word i*GQ + q
 #pragma unroll
-      for (int b = 0; b < G; ++b) {
-        const int q = b >> 2, bb = b & 3;
-        uint32_t v[4];
+        for (int i = 0; i < 4; ++i) ow[i] = own[i * GQ + q];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = __byte_perm(ow[i * GQ + q], 0u, 0x4440u + bb);
-        chunk_scan32(v, lane);
-        const uint32_t lown = my_ctot[(size_t)c * G + b];
-        if (publish)
-          *reinterpret_cast<uint4 *>(f.incl + ((size_t)ci * G + b) * kChunk + 4 * lane) =
-              make_uint4(acc[b][0] + v[0] + lown, acc[b][1] + v[1] + lown,
-                         acc[b][2] + v[2] + lown, acc[b][3] + v[3] + lown);
+        for (int bb = 0; bb < 4; ++bb) {
+          const int b = 4 * q + bb;
+          uint32_t v[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) v[i] = __byte_perm(ow[i], 0u, 0x4440u + bb);
+          chunk_scan32(v, lane);
+          const uint32_t lown = my_ctot[(size_t)c * G + b];
+          if (publish)
+            *reinterpret_cast<uint4 *>(f.incl + ((size_t)ci * G + b) * kChunk + 4 * lane) =
+                make_uint4(acc[b][0] + v[0] + lown, acc[b][1] + v[1] + lown,
+                           acc[b][2] + v[2] + lown, acc[b][3] + v[3] + lown);
+        }
       }
       __threadfence();
       __syncwarp();

@@ -207,6 +207,9 @@ class FakeExecutor:
     def release(self, rid, payload):
         pass
 
+    def finish(self, handle):
+        pass
+
 
 class Server:
     """Continuous-batching request loop over an executor (see module doc)."""
@@ -320,6 +323,7 @@ class Server:
                         if self.keep_results:
                             r = h.get("result")
                             self.results[obj.rid] = r.clone() if hasattr(r, "clone") else r
+                        self.ex.finish(h)  # the executor may now reuse the result's buffers
                         self.done.append(Done(obj.rid, kind, obj.t_arrival, td, target=obj.target,
                                               t_launch=h["t_launch"]))
                 else:
@@ -431,7 +435,7 @@ class GpuExecutor:
     """
 
     def __init__(self, mode="batched", nslots=64, max_shape=(1080, 1920, 64), query_slots=8, max_rects=10000,
-                 trace=False):
+                 trace=False, keep_results=True):
         """trace: mark every launch with an NVTX range (frames / query, with
         sizes) so a profiler's timeline shows the serving loop's issue."""
         import torch
@@ -439,6 +443,7 @@ class GpuExecutor:
         from . import ihist
         self.torch, self.ih = torch, ihist
         self.mode = mode
+        self.keep_results = keep_results  # the server reads query results (copy them before a slot is reused)
         self.trace = trace
         self.stream = torch.cuda.current_stream()
         self.copy = torch.cuda.Stream()
@@ -453,7 +458,10 @@ class GpuExecutor:
             for _ in range(2):
                 ins = [torch.empty((h, w), dtype=torch.uint8, device="cuda") for _ in range(nslots)]
                 outs = [torch.empty((b, h, w), dtype=torch.int32, device="cuda") for _ in range(1)] * nslots
-                self.batches.append(ihist.Batch(ins, b, outs=outs))
+                # one CTA slot per SM stays free, so a query launched on the
+                # high-priority stream starts while a batch is running instead
+                # of waiting for the whole persistent launch to end
+                self.batches.append(ihist.Batch(ins, b, outs=outs, tune={"ctas_per_sm": 3}))
                 self.inputs.append(ins)
             del outs
         self.next_batch = 0
@@ -467,18 +475,45 @@ class GpuExecutor:
         # query slots, reused round robin: pinned and device buffers for the
         # rectangles and the rows, so that issuing a query allocates nothing
         self.max_rects = max_rects
-        self.qslots = []
-        for _ in range(query_slots):
-            self.qslots.append({
-                "h_rects": torch.empty((max_rects, 4), dtype=torch.int32, pin_memory=True),
-                "d_rects": torch.empty((max_rects, 4), dtype=torch.int32, device="cuda"),
-                "d_out": torch.empty((max_rects * 256,), dtype=torch.int32, device="cuda"),
-                "h_out": torch.empty((max_rects * 256,), dtype=torch.int32, pin_memory=True),
-                "d_best": torch.zeros((1,), dtype=torch.int64, device="cuda"),
-                "h_best": torch.zeros((1,), dtype=torch.int64, pin_memory=True),
-                "free": None,  # event: the slot's last rows have reached the host
-            })
+        self.qslots = [self._new_qslot() for _ in range(query_slots)]
         self.next_qslot = 0
+
+    def _new_qslot(self):
+        torch = self.torch
+        m = self.max_rects
+        return {
+            "h_rects": torch.empty((m, 4), dtype=torch.int32, pin_memory=True),
+            "d_rects": torch.empty((m, 4), dtype=torch.int32, device="cuda"),
+            "d_out": torch.empty((m * 256,), dtype=torch.int32, device="cuda"),
+            "h_out": torch.empty((m * 256,), dtype=torch.int32, pin_memory=True),
+            "d_best": torch.zeros((1,), dtype=torch.int64, device="cuda"),
+            "h_best": torch.zeros((1,), dtype=torch.int64, pin_memory=True),
+            "free": None,   # event: the slot's last rows have reached the host
+            "owner": None,  # handle whose result the slot holds until the server takes it
+        }
+
+    def _take_qslot(self):
+        """The next query slot, round robin over a fixed pool.  Its previous
+        request's rows must be on the host (wait for its event, rarely
+        needed) and, if the server has not taken that result yet, they are
+        copied into the request's handle first, so reuse never changes a
+        result the server will read."""
+        slot = self.qslots[self.next_qslot]
+        self.next_qslot = (self.next_qslot + 1) % len(self.qslots)
+        if slot["free"] is not None:
+            slot["free"].synchronize()
+        owner = slot["owner"]
+        if owner is not None and self.keep_results:
+            owner["result"] = owner["result"].clone()
+        slot["owner"] = None
+        return slot
+
+    def finish(self, handle):
+        """The server has taken the handle's result: its query slot no longer
+        holds a result anyone will read."""
+        slot = handle.get("slot")
+        if slot is not None and slot["owner"] is handle:
+            slot["owner"] = None
 
     def warm(self, shapes):
         """Create the per-shape plans and run every kernel once before
@@ -539,9 +574,10 @@ class GpuExecutor:
             b = self.batches[self.next_batch]
             ins = self.inputs[1 + self.next_batch]
             self.next_batch ^= 1
-            views = [ins[i].view(-1)[:r.h * r.w].view(r.h, r.w) for i, r in enumerate(reqs)]
-            b.set_io(views, [outs[r.rid] for r in reqs], nbins=[r.nbins for r in reqs],
-                     layouts=[0] * len(reqs), stream=self.s)
+            # bind the slots with raw pointers (rows packed at the frame's
+            # width in each slot buffer): no tensor views on the issue path
+            ih.ihist_batch_set_io(b.handle, [(r.h, r.w, r.nbins, 0, ins[i].data_ptr(), r.w, outs[r.rid].data_ptr())
+                                             for i, r in enumerate(reqs)], self.s)
             ih.ihist_batch_upload_compute(b.handle, [r.frame.data_ptr() for r in reqs], self.s,
                                           self.copy.cuda_stream)
         else:
@@ -555,7 +591,8 @@ class GpuExecutor:
                 view.copy_(r.frame, non_blocking=True)
                 self.upload_done[k].record(self.copy)
             self.stream.wait_event(self.upload_done[k])
-            self._plan(r.h, r.w, r.nbins).compute(view, outs[r.rid], stream=self.s)
+            # the plan's entry point with raw pointers (the shapes were checked at admission)
+            ih.ihist_compute(self._plan(r.h, r.w, r.nbins).handle, view.data_ptr(), r.w, outs[r.rid].data_ptr(), self.s)
             self.read_done[k].record(self.stream)
         ev.record(self.stream)
         return {"ev": ev, "payloads": {r.rid: (outs[r.rid], r.h, r.w, r.nbins) for r in reqs}}
@@ -583,10 +620,7 @@ class GpuExecutor:
         # search keeps only the best window; 8 bytes come back
         torch, ih = self.torch, self.ih
         hist, h, w, b = payload
-        slot = self.qslots[self.next_qslot]
-        self.next_qslot = (self.next_qslot + 1) % len(self.qslots)
-        if slot["free"] is not None:
-            slot["free"].synchronize()
+        slot = self._take_qslot()
         slot["h_rects"].numpy()[0] = (q.x, q.y, q.x + q.win_w - 1, q.y + q.win_h - 1)
         qs = self.qstream.cuda_stream
         plan = self._plan(h, w, b)
@@ -600,7 +634,10 @@ class GpuExecutor:
             ev.record(self.qstream)
         slot["free"] = ev
         hist.record_stream(self.qstream)
-        return {"ev": ev, "result": slot["h_best"], "nx": ih.window_grid(h, w, q.win_h, q.win_w, q.stride)[1]}
+        handle = {"ev": ev, "result": slot["h_best"], "slot": slot,
+                  "nx": ih.window_grid(h, w, q.win_h, q.win_w, q.stride)[1]}
+        slot["owner"] = handle
+        return handle
 
     def _launch_query(self, q, payload, t):
         # the server launches a query only once its histogram is complete,
@@ -610,10 +647,7 @@ class GpuExecutor:
         n = len(q.rects)
         if n > self.max_rects:
             raise ValueError("query of %d rectangles exceeds the executor's %d" % (n, self.max_rects))
-        slot = self.qslots[self.next_qslot]
-        self.next_qslot = (self.next_qslot + 1) % len(self.qslots)
-        if slot["free"] is not None:
-            slot["free"].synchronize()  # the slot's previous rows are on the host (rarely waits)
+        slot = self._take_qslot()
         slot["h_rects"].numpy()[:n] = q.rects
         qs = self.qstream.cuda_stream
         d_rects, d_out, h_out = slot["d_rects"], slot["d_out"], slot["h_out"]
@@ -625,7 +659,9 @@ class GpuExecutor:
             ev.record(self.qstream)
         slot["free"] = ev
         hist.record_stream(self.qstream)
-        return {"ev": ev, "result": h_out[:n * b].view(n, b)}
+        handle = {"ev": ev, "result": h_out[:n * b].view(n, b), "slot": slot}
+        slot["owner"] = handle
+        return handle
 
     def poll(self, handle, t):
         return handle["ev"].query()
@@ -657,7 +693,7 @@ def serve(mode="batched", duration_s=2.0, budget_gb=40.0, seed=None, frame_rate=
         # the same requests, arriving 1000 times faster than the server can take them
         for r in reqs:
             r.t_arrival *= 1e-3
-    ex = GpuExecutor(mode, max_rects=max(1, rects_per_query), trace=trace)
+    ex = GpuExecutor(mode, max_rects=max(1, rects_per_query), trace=trace, keep_results=False)
     ex.warm(sorted({(r.h, r.w, r.nbins) for r in reqs if isinstance(r, FrameRequest)}))
     srv = Server(ex, int(budget_gb * (1 << 30)), mode=mode, keep_results=False)
     ex.start()

@@ -153,3 +153,37 @@ def test_decode_best():
     assert serve.decode_best(0, 10) is None
     v = (4096 << 32) | (0xffffffff - 23)
     assert serve.decode_best(v, 10) == (4096, 2, 3)
+
+
+class _Ev:
+    def synchronize(self):
+        pass
+
+
+class _Rows:
+    """A result that views a slot's host buffer (clone copies it)."""
+
+    def __init__(self, buf):
+        self.buf = buf
+
+    def clone(self):
+        return _Rows(list(self.buf))
+
+
+def test_query_slot_reuse_keeps_results_the_server_has_not_taken():
+    ex = object.__new__(serve.GpuExecutor)  # only the slot bookkeeping, no GPU
+    ex.keep_results = True
+    ex.qslots = [{"free": None, "owner": None, "buf": [0]}, {"free": None, "owner": None, "buf": [0]}]
+    ex.next_qslot = 0
+    handles = []
+    for value in (11, 22, 33):  # the third request reuses the first one's slot
+        slot = ex._take_qslot()
+        slot["buf"][0] = value  # the request's rows land in the slot's host buffer
+        h = {"result": _Rows(slot["buf"]), "slot": slot}
+        slot["owner"] = h
+        slot["free"] = _Ev()
+        handles.append(h)
+    assert [h["result"].buf[0] for h in handles] == [11, 22, 33]  # the first result was copied out
+    ex.finish(handles[1])
+    slot = ex._take_qslot()  # the second slot: its result was taken, nothing to copy
+    assert slot["owner"] is None and handles[1]["result"].buf is slot["buf"]
