@@ -126,7 +126,7 @@ def profiled_traffic(path=PROFILE):
         kv = {}
         for line in open(path):
             if "=" in line and not line.lstrip().startswith("#"):
-                k, v = line.split("=", 1)
+                k, v = line.split("#", 1)[0].split("=", 1)
                 kv[k.strip()] = v.strip()
         if kv.get("scan_source_sha256_16") != scan_source_hash():
             return None
@@ -418,7 +418,7 @@ def serving_report(seconds: float) -> dict:
     faster than they can be served."""
     from paper_1711_01919_gb300 import serve
 
-    keep = ("completed", "rejected", "p50_ms", "p99_ms", "per_s", "launch_wait_p99_ms")
+    keep = ("completed", "rejected", "p50_ms", "p99_ms", "max_ms", "per_s", "launch_wait_p99_ms")
     out = {"workload": "Poisson arrivals for %.1f s: frames at 2000/s (320x240..1920x1080, 16-64 bins), "
                        "queries of 10,000 rects at 200/s and searches for a 64x64 patch (stride 8) at 50/s "
                        "against a random resident histogram; 40 GB budget, LRU eviction" % seconds}
@@ -435,7 +435,7 @@ def serving_report(seconds: float) -> dict:
         out[mode]["host_issue_p50_ms"] = rep["host_issue_p50_ms"]
         out[mode]["evicted"] = rep["evicted"]
     for mode in ("batched", "plain"):
-        rep = serve.serve(mode=mode, duration_s=seconds / 4, saturate=True)
+        rep = serve.serve(mode=mode, duration_s=seconds / 2, saturate=True)
         out["saturated_" + mode] = {"frames_per_s": rep["frame"]["per_s"], "frames": rep["frame"]["completed"],
                                     "frame_p99_ms": rep["frame"]["p99_ms"]}
     return out

@@ -26,10 +26,11 @@ compute.  Queries whose histogram is ready are launched as they come.
 Latency is taken from GPU event timestamps against a reference event
 recorded at the start, so it does not depend on how often the host polls.
 
-When fewer than ``min_batch`` frames are waiting, the batched server
+When fewer than ``min_batch`` (8) frames are waiting, the batched server
 launches them one by one (``ihist_compute`` with a per-shape plan): a short
 queue gains nothing from a shared launch, whose first frame would wait for
-the others.  Queries run on a stream of their own, so they do not
+the others (at 2000 frames/s a threshold of 4 still sent 4-6 bursts per 10 s
+through shared launches, and their frames set the p99).  Queries run on a stream of their own, so they do not
 queue behind frames that do not concern them.
 
 ``mode="plain"`` serves every frame with its own ``ihist_compute`` launch
@@ -109,31 +110,39 @@ def frame_supported(h: int, w: int, nbins: int) -> bool:
 
 
 class HistStore:
-    """Resident histograms under a byte budget; LRU over entries not pinned."""
+    """Resident histograms under a byte budget; LRU over entries not pinned.
+    `evictable` (bytes of entries that are ready and not pinned) is kept up
+    to date by every change, so admission costs O(1) however many
+    histograms are resident."""
 
     def __init__(self, budget: int):
         self.budget = budget
         self.used = 0
+        self.evictable = 0
         self.entries = collections.OrderedDict()  # rid -> [bytes, pins, ready, payload]
         self.evicted = 0
 
     def can_fit(self, nbytes: int) -> bool:
-        if self.used + nbytes <= self.budget:
-            return True
-        free = sum(e[0] for e in self.entries.values() if e[1] == 0 and e[2])
-        return self.used - free + nbytes <= self.budget
+        return self.used - self.evictable + nbytes <= self.budget
 
     def reserve(self, rid: int, nbytes: int, evict_cb=None) -> bool:
-        """Make room (evicting LRU unpinned ready entries) and reserve nbytes."""
+        """Make room (evicting LRU unpinned ready entries) and reserve nbytes.
+        Walks the LRU order only as far as it must (usually one or two
+        entries), not over every resident histogram."""
         if not self.can_fit(nbytes):
             return False
-        for k in list(self.entries.keys()):
-            if self.used + nbytes <= self.budget:
-                break
-            e = self.entries[k]
-            if e[1] == 0 and e[2]:
+        if self.used + nbytes > self.budget:
+            victims, freed = [], 0
+            for k, e in self.entries.items():
+                if self.used - freed + nbytes <= self.budget:
+                    break
+                if e[1] == 0 and e[2]:
+                    victims.append(k)
+                    freed += e[0]
+            for k in victims:
+                e = self.entries.pop(k)
                 self.used -= e[0]
-                del self.entries[k]
+                self.evictable -= e[0]
                 self.evicted += 1
                 if evict_cb:
                     evict_cb(k, e[3])
@@ -146,6 +155,8 @@ class HistStore:
     def set_ready(self, rid: int, payload=None):
         e = self.entries.get(rid)
         if e is not None:
+            if not e[2] and e[1] == 0:
+                self.evictable += e[0]
             e[2] = True
             if payload is not None:
                 e[3] = payload
@@ -155,12 +166,18 @@ class HistStore:
             self.entries.move_to_end(rid)
 
     def pin(self, rid: int):
-        self.entries[rid][1] += 1
+        e = self.entries[rid]
+        if e[1] == 0 and e[2]:
+            self.evictable -= e[0]
+        e[1] += 1
         self.touch(rid)
 
     def unpin(self, rid: int):
-        if rid in self.entries:
-            self.entries[rid][1] -= 1
+        e = self.entries.get(rid)
+        if e is not None:
+            e[1] -= 1
+            if e[1] == 0 and e[2]:
+                self.evictable += e[0]
 
     def resident(self):
         return list(self.entries.keys())
@@ -215,7 +232,7 @@ class Server:
     """Continuous-batching request loop over an executor (see module doc)."""
 
     def __init__(self, executor, budget_bytes: int, max_batch: int = 64, mode: str = "batched",
-                 seed: int = 4, min_batch: int = 4, keep_results: bool = True):
+                 seed: int = 4, min_batch: int = 8, keep_results: bool = True):
         self.ex = executor
         self.store = HistStore(budget_bytes)
         self.max_batch = max_batch if mode == "batched" else 1
@@ -444,6 +461,7 @@ class GpuExecutor:
         self.torch, self.ih = torch, ihist
         self.mode = mode
         self.keep_results = keep_results  # the server reads query results (copy them before a slot is reused)
+        self.free_outputs = {}  # (h, w, b) -> evicted output buffers for reuse
         self.trace = trace
         self.stream = torch.cuda.current_stream()
         self.copy = torch.cuda.Stream()
@@ -568,7 +586,7 @@ class GpuExecutor:
 
     def _launch_frames(self, reqs, t):
         torch, ih = self.torch, self.ih
-        outs = {r.rid: torch.empty((r.nbins, r.h, r.w), dtype=torch.int32, device="cuda") for r in reqs}
+        outs = {r.rid: self._output(r.h, r.w, r.nbins) for r in reqs}
         ev = torch.cuda.Event(enable_timing=True)
         if self.mode == "batched" and len(reqs) > 1:
             b = self.batches[self.next_batch]
@@ -669,8 +687,23 @@ class GpuExecutor:
     def done_time(self, handle):
         return self.t0_event.elapsed_time(handle["ev"]) / 1e3
 
+    def _output(self, h, w, b):
+        """An output buffer for a (h, w, b) histogram: an evicted one of the
+        same shape if there is one, else a new allocation.  Reusing evicted
+        buffers keeps torch's allocator (whose cudaMalloc / cudaFree can
+        stall the host) out of the serving loop once the shapes have been
+        seen."""
+        free = self.free_outputs.get((h, w, b))
+        if free:
+            return free.pop()
+        return self.torch.empty((b, h, w), dtype=self.torch.int32, device="cuda")
+
     def release(self, rid, payload):
-        pass  # dropping the last reference returns the memory to torch's allocator
+        # an evicted histogram has no pending query (queries pin their
+        # targets) and its compute has completed, so its buffer can take the
+        # next histogram of the same shape on the compute stream
+        hist, h, w, b = payload
+        self.free_outputs.setdefault((h, w, b), []).append(hist)
 
     def close(self):
         for b in self.batches:

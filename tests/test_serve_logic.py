@@ -187,3 +187,31 @@ def test_query_slot_reuse_keeps_results_the_server_has_not_taken():
     ex.finish(handles[1])
     slot = ex._take_qslot()  # the second slot: its result was taken, nothing to copy
     assert slot["owner"] is None and handles[1]["result"].buf is slot["buf"]
+
+
+def test_store_evictable_bytes_track_every_change():
+    # the running count of evictable bytes (ready, unpinned) equals a full
+    # recount after any sequence of reserve / ready / pin / unpin / eviction
+    rng = np.random.default_rng(5)
+    store = serve.HistStore(budget_bytes := 10_000)
+    evicted = []
+    live = []
+    for step in range(3000):
+        op = rng.integers(4)
+        if op == 0:
+            rid = step
+            if store.reserve(rid, int(rng.integers(100, 900)), lambda k, p: evicted.append(k)):
+                live.append(rid)
+        elif op == 1 and live:
+            store.set_ready(live[int(rng.integers(len(live)))], payload=("h",))
+        elif op == 2 and store.ready_ids():
+            store.pin(store.ready_ids()[int(rng.integers(len(store.ready_ids())))])
+        elif op == 3:
+            pinned = [k for k, e in store.entries.items() if e[1] > 0]
+            if pinned:
+                store.unpin(pinned[int(rng.integers(len(pinned)))])
+        live = [k for k in live if k in store.entries]
+        want = sum(e[0] for e in store.entries.values() if e[1] == 0 and e[2])
+        assert store.evictable == want, step
+        assert store.used == sum(e[0] for e in store.entries.values()) <= budget_bytes
+    assert evicted
