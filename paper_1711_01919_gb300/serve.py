@@ -111,41 +111,44 @@ def frame_supported(h: int, w: int, nbins: int) -> bool:
 
 class HistStore:
     """Resident histograms under a byte budget; LRU over entries not pinned.
-    `evictable` (bytes of entries that are ready and not pinned) is kept up
-    to date by every change, so admission costs O(1) however many
-    histograms are resident."""
+    The entries that may be evicted (ready, not pinned) are also kept in an
+    LRU-ordered dict of their own, with their total bytes, so admission and
+    eviction cost O(1) however many histograms are resident or waiting (a
+    full store at saturation holds hundreds of admitted frames not yet
+    computed)."""
 
     def __init__(self, budget: int):
         self.budget = budget
         self.used = 0
         self.evictable = 0
-        self.entries = collections.OrderedDict()  # rid -> [bytes, pins, ready, payload]
+        self.entries = collections.OrderedDict()  # rid -> [bytes, pins, ready, payload], LRU order
+        self.lru = collections.OrderedDict()      # the evictable rids, LRU order
         self.evicted = 0
 
     def can_fit(self, nbytes: int) -> bool:
         return self.used - self.evictable + nbytes <= self.budget
 
+    def _add_evictable(self, rid, e):
+        self.lru[rid] = None
+        self.evictable += e[0]
+
+    def _drop_evictable(self, rid, e):
+        if self.lru.pop(rid, 0) is None:
+            self.evictable -= e[0]
+
     def reserve(self, rid: int, nbytes: int, evict_cb=None) -> bool:
-        """Make room (evicting LRU unpinned ready entries) and reserve nbytes.
-        Walks the LRU order only as far as it must (usually one or two
-        entries), not over every resident histogram."""
+        """Make room (evicting the least recently used ready, unpinned
+        entries) and reserve nbytes."""
         if not self.can_fit(nbytes):
             return False
-        if self.used + nbytes > self.budget:
-            victims, freed = [], 0
-            for k, e in self.entries.items():
-                if self.used - freed + nbytes <= self.budget:
-                    break
-                if e[1] == 0 and e[2]:
-                    victims.append(k)
-                    freed += e[0]
-            for k in victims:
-                e = self.entries.pop(k)
-                self.used -= e[0]
-                self.evictable -= e[0]
-                self.evicted += 1
-                if evict_cb:
-                    evict_cb(k, e[3])
+        while self.used + nbytes > self.budget and self.lru:
+            k, _ = self.lru.popitem(last=False)
+            e = self.entries.pop(k)
+            self.used -= e[0]
+            self.evictable -= e[0]
+            self.evicted += 1
+            if evict_cb:
+                evict_cb(k, e[3])
         if self.used + nbytes > self.budget:
             return False
         self.entries[rid] = [nbytes, 0, False, None]
@@ -156,7 +159,7 @@ class HistStore:
         e = self.entries.get(rid)
         if e is not None:
             if not e[2] and e[1] == 0:
-                self.evictable += e[0]
+                self._add_evictable(rid, e)
             e[2] = True
             if payload is not None:
                 e[3] = payload
@@ -164,11 +167,13 @@ class HistStore:
     def touch(self, rid: int):
         if rid in self.entries:
             self.entries.move_to_end(rid)
+            if rid in self.lru:
+                self.lru.move_to_end(rid)
 
     def pin(self, rid: int):
         e = self.entries[rid]
         if e[1] == 0 and e[2]:
-            self.evictable -= e[0]
+            self._drop_evictable(rid, e)
         e[1] += 1
         self.touch(rid)
 
@@ -177,7 +182,7 @@ class HistStore:
         if e is not None:
             e[1] -= 1
             if e[1] == 0 and e[2]:
-                self.evictable += e[0]
+                self._add_evictable(rid, e)
 
     def resident(self):
         return list(self.entries.keys())
@@ -357,6 +362,7 @@ class Server:
             lat = np.array([d.t_done - d.t_arrival for d in ok]) * 1e3
             wait = np.array([d.t_launch - d.t_arrival for d in ok]) * 1e3  # host: arrival -> launched
             out[kind] = {
+                "latencies_ms": lat,  # every completed request's latency (for pooling runs)
                 "completed": len(ok),
                 "rejected": sum(1 for d in self.done if d.kind == kind and d.status != "ok"),
                 "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,

@@ -190,8 +190,9 @@ def test_query_slot_reuse_keeps_results_the_server_has_not_taken():
 
 
 def test_store_evictable_bytes_track_every_change():
-    # the running count of evictable bytes (ready, unpinned) equals a full
-    # recount after any sequence of reserve / ready / pin / unpin / eviction
+    # the running count of evictable bytes (ready, unpinned) and the set of
+    # evictable entries equal a full recount after any sequence of reserve /
+    # ready / pin / unpin / eviction
     rng = np.random.default_rng(5)
     store = serve.HistStore(budget_bytes := 10_000)
     evicted = []
@@ -213,5 +214,6 @@ def test_store_evictable_bytes_track_every_change():
         live = [k for k in live if k in store.entries]
         want = sum(e[0] for e in store.entries.values() if e[1] == 0 and e[2])
         assert store.evictable == want, step
+        assert set(store.lru) == {k for k, e in store.entries.items() if e[1] == 0 and e[2]}, step
         assert store.used == sum(e[0] for e in store.entries.values()) <= budget_bytes
     assert evicted
