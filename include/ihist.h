@@ -393,7 +393,9 @@ int ihist_batch_get_tune(ihist_batch_t batch, ihist_tune_t *out);
  * larger (same or smaller height, width and bin count always do);
  * otherwise IHIST_ERR_UNSUPPORTED and the previous binding stays.  The new
  * descriptors are copied on `stream`, so later launches on it see them; the
- * call may wait for this batch's previous descriptor copy to finish.
+ * descriptors are staged in one of two pinned buffers used by alternate
+ * bindings, so the call waits (on the host) only for the copy made two
+ * bindings earlier, and a caller may bind and launch ahead of the GPU.
  * Nothing is allocated. */
 int ihist_batch_set_io(ihist_batch_t batch, const ihist_frame_t *frames, int n, void *stream);
 

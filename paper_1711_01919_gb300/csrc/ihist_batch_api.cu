@@ -178,11 +178,22 @@ struct ihist_batch_s {
   std::vector<uint8_t *> slot_idx;
   std::vector<FrameDesc> fd;                          // current frames
   std::vector<ihist_frame_t> io;
-  FrameDesc *h_fd, *h_fdq;   // pinned staging
+  // Pinned staging of the descriptors, two sets used by alternate bindings:
+  // a binding waits only for the copy made from its set two bindings ago,
+  // so a caller can bind and launch ahead of the GPU.  h_* point at the set
+  // of the binding being built; staged[i] marks set i's last copy done.
+  struct Staging {
+    FrameDesc *fd, *fdq;
+    CUtensorMap *tm;
+    unsigned int *end, *bins_end;
+    uint32_t *lut;
+  } stage_sets[2];
+  cudaEvent_t staged[2];
+  int stage_cur;
+  FrameDesc *h_fd, *h_fdq;
   CUtensorMap *h_tm;
   unsigned int *h_end, *h_bins_end;
   uint32_t *h_lut;
-  cudaEvent_t staged;        // last staging copy done
   cudaEvent_t uploaded, computed;
   bool launched;
 };
@@ -198,6 +209,17 @@ static bool encode_frame_map(const uint8_t *in, size_t pitch, int h, int w, int 
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(in), gdim, gstride,
              box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Point h_* at staging set i.
+static void use_staging(ihist_batch_s *b, int i) {
+  b->stage_cur = i;
+  b->h_fd = b->stage_sets[i].fd;
+  b->h_fdq = b->stage_sets[i].fdq;
+  b->h_tm = b->stage_sets[i].tm;
+  b->h_end = b->stage_sets[i].end;
+  b->h_bins_end = b->stage_sets[i].bins_end;
+  b->h_lut = b->stage_sets[i].lut;
 }
 
 // Tile the given frames into the plan's slots and fill the pinned staging
@@ -295,7 +317,7 @@ static int batch_upload(ihist_batch_s *b, cudaStream_t s) {
           cudaSuccess ||
       (b->lut && cudaMemcpyAsync(b->d_lut, b->h_lut, (size_t)n * 256 * sizeof(uint32_t), cudaMemcpyHostToDevice,
                                  s) != cudaSuccess) ||
-      cudaEventRecord(b->staged, s) != cudaSuccess)
+      cudaEventRecord(b->staged[b->stage_cur], s) != cudaSuccess)
     return IHIST_ERR_CUDA;
   return IHIST_OK;
 }
@@ -305,16 +327,21 @@ extern "C" void ihist_batch_destroy(ihist_batch_t b) {
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != b->device) cudaSetDevice(b->device);
-  if (b->staged) cudaEventSynchronize(b->staged);
-  if (b->staged) cudaEventDestroy(b->staged);
+  for (int i = 0; i < 2; ++i) {
+    if (b->staged[i]) cudaEventSynchronize(b->staged[i]);
+    if (b->staged[i]) cudaEventDestroy(b->staged[i]);
+  }
   if (b->uploaded) cudaEventDestroy(b->uploaded);
   if (b->computed) cudaEventDestroy(b->computed);
-  if (b->h_fd) cudaFreeHost(b->h_fd);
-  if (b->h_fdq) cudaFreeHost(b->h_fdq);
-  if (b->h_tm) cudaFreeHost(b->h_tm);
-  if (b->h_end) cudaFreeHost(b->h_end);
-  if (b->h_bins_end) cudaFreeHost(b->h_bins_end);
-  if (b->h_lut) cudaFreeHost(b->h_lut);
+  for (int i = 0; i < 2; ++i) {
+    ihist_batch_s::Staging &st = b->stage_sets[i];
+    if (st.fd) cudaFreeHost(st.fd);
+    if (st.fdq) cudaFreeHost(st.fdq);
+    if (st.tm) cudaFreeHost(st.tm);
+    if (st.end) cudaFreeHost(st.end);
+    if (st.bins_end) cudaFreeHost(st.bins_end);
+    if (st.lut) cudaFreeHost(st.lut);
+  }
   if (b->ws) cudaFree(b->ws);
   if (prev != b->device && prev >= 0) cudaSetDevice(prev);
   delete b;
@@ -523,13 +550,20 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
   }
   b->ws_bytes = off;
   if (cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess ||
-      cudaMallocHost((void **)&b->h_fd, (size_t)n * sizeof(FrameDesc)) != cudaSuccess ||
-      cudaMallocHost((void **)&b->h_fdq, (size_t)n * sizeof(FrameDesc)) != cudaSuccess ||
-      cudaMallocHost((void **)&b->h_tm, (size_t)n * sizeof(CUtensorMap)) != cudaSuccess ||
-      cudaMallocHost((void **)&b->h_end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
-      cudaMallocHost((void **)&b->h_bins_end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
-      (lut && cudaMallocHost((void **)&b->h_lut, (size_t)n * 256 * sizeof(uint32_t)) != cudaSuccess) ||
-      cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess ||
+      [&]() {
+        for (int i = 0; i < 2; ++i) {
+          ihist_batch_s::Staging &st = b->stage_sets[i];
+          if (cudaMallocHost((void **)&st.fd, (size_t)n * sizeof(FrameDesc)) != cudaSuccess ||
+              cudaMallocHost((void **)&st.fdq, (size_t)n * sizeof(FrameDesc)) != cudaSuccess ||
+              cudaMallocHost((void **)&st.tm, (size_t)n * sizeof(CUtensorMap)) != cudaSuccess ||
+              cudaMallocHost((void **)&st.end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
+              cudaMallocHost((void **)&st.bins_end, (size_t)n * sizeof(unsigned int)) != cudaSuccess ||
+              (lut && cudaMallocHost((void **)&st.lut, (size_t)n * 256 * sizeof(uint32_t)) != cudaSuccess) ||
+              cudaEventCreateWithFlags(&b->staged[i], cudaEventDisableTiming) != cudaSuccess)
+            return false;
+        }
+        return true;
+      }() == false ||
       cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->computed, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -565,6 +599,7 @@ extern "C" int ihist_batch_plan(const ihist_frame_t *frames, int n, const ihist_
     b->slot_idx.push_back(b->slot_idx_cap[i] ? reinterpret_cast<uint8_t *>(base + xo) : nullptr);
     xo = align_up(xo + b->slot_idx_cap[i], 256);
   }
+  use_staging(b, 0);
   int rc = batch_bind(b, frames, n);
   if (rc != IHIST_OK) {
     ihist_batch_destroy(b);
@@ -607,10 +642,17 @@ extern "C" int ihist_batch_set_io(ihist_batch_t b, const ihist_frame_t *frames, 
   if (!b || !frames) return IHIST_ERR_INVALID_ARG;
   int rc = check_batch_device(b);
   if (rc != IHIST_OK) return rc;
-  // the staging buffers may still feed the previous copy
-  if (cudaEventSynchronize(b->staged) != cudaSuccess) return IHIST_ERR_CUDA;
+  // build the binding in the other staging set, once that set's previous
+  // copy (two bindings back) has been made; on failure the current binding
+  // (already copied from its own set) stays in force
+  const int prev = b->stage_cur, next = prev ^ 1;
+  if (cudaEventSynchronize(b->staged[next]) != cudaSuccess) return IHIST_ERR_CUDA;
+  use_staging(b, next);
   rc = batch_bind(b, frames, n);
-  if (rc != IHIST_OK) return rc;
+  if (rc != IHIST_OK) {
+    use_staging(b, prev);
+    return rc;
+  }
   return batch_upload(b, (cudaStream_t)stream);
 }
 

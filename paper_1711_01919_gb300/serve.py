@@ -479,7 +479,11 @@ class GpuExecutor:
         self.inputs = []
         self.inputs.append([torch.empty((h, w), dtype=torch.uint8, device="cuda") for _ in range(2)])
         if mode == "batched":
-            for _ in range(2):
+            # a ring of 4 batches: binding a batch waits (on the host) for its
+            # previous descriptor copy, so with 4 the host can run that many
+            # launches ahead of the GPU before it waits (2 measured host-bound
+            # at saturation)
+            for _ in range(4):
                 ins = [torch.empty((h, w), dtype=torch.uint8, device="cuda") for _ in range(nslots)]
                 outs = [torch.empty((b, h, w), dtype=torch.int32, device="cuda") for _ in range(1)] * nslots
                 # one CTA slot per SM stays free, so a query launched on the
@@ -597,7 +601,7 @@ class GpuExecutor:
         if self.mode == "batched" and len(reqs) > 1:
             b = self.batches[self.next_batch]
             ins = self.inputs[1 + self.next_batch]
-            self.next_batch ^= 1
+            self.next_batch = (self.next_batch + 1) % len(self.batches)
             # bind the slots with raw pointers (rows packed at the frame's
             # width in each slot buffer): no tensor views on the issue path
             ih.ihist_batch_set_io(b.handle, [(r.h, r.w, r.nbins, 0, ins[i].data_ptr(), r.w, outs[r.rid].data_ptr())
