@@ -237,7 +237,7 @@ class Server:
     """Continuous-batching request loop over an executor (see module doc)."""
 
     def __init__(self, executor, budget_bytes: int, max_batch: int = 64, mode: str = "batched",
-                 seed: int = 4, min_batch: int = 8, keep_results: bool = True):
+                 seed: int = 4, min_batch: int = 8, keep_results: bool = True, hold: int = 2):
         self.ex = executor
         self.store = HistStore(budget_bytes)
         self.max_batch = max_batch if mode == "batched" else 1
@@ -245,6 +245,9 @@ class Server:
         # queue gains nothing from a shared launch, and the first frame of a
         # batch would wait for the others
         self.min_batch = min_batch if mode == "batched" else 1
+        # frame launches in flight from which waiting frames are held back to
+        # fill a whole shared launch (batched mode only)
+        self.hold = hold if mode == "batched" else 1 << 30
         self.mode = mode
         self.rng = np.random.default_rng(seed)
         self.done = []
@@ -316,8 +319,14 @@ class Server:
                     inflight.append((h, _kind(q), q))
                 else:
                     waiting_queries.append(q)
-            # 4. one batched launch of everything admitted (continuous batching)
+            # 4. frame launches (continuous batching).  While `hold` or more
+            # frame launches are in flight the GPU has work queued, so admitted
+            # frames wait to fill a whole shared launch; otherwise they go out
+            # at once: one by one if fewer than min_batch wait, else together
+            frame_launches = sum(1 for _, kind, _ in inflight if kind == "frames")
             while ready_frames:
+                if frame_launches >= self.hold and len(ready_frames) < self.max_batch:
+                    break
                 take = self.max_batch if len(ready_frames) >= self.min_batch else 1
                 batch, ready_frames = ready_frames[:take], ready_frames[take:]
                 t_call = clock()
@@ -326,6 +335,7 @@ class Server:
                 self.host_ms["frames"].append(1e3 * (h["t_launch"] - t_call))
                 self.batch_sizes[len(batch)] += 1
                 inflight.append((h, "frames", batch))
+                frame_launches += 1
                 if len(batch) > 1:
                     break  # one shared launch per iteration; later arrivals join the next
             # 5. completions
@@ -446,15 +456,15 @@ def serving_workload(seed: int, duration_s: float, frame_rate: float = 2000.0, q
 class GpuExecutor:
     """Runs the server's launches with libihist on one GPU.
 
-    batched: `nslots`-frame batch plans (two, alternating) whose slots are
+    batched: a ring of four `nslots`-frame batch plans whose slots are
     sized for the largest frame of the mix; every launch of two or more
     frames rebinds the slots to the admitted frames (ihist_batch_set_io) and
     uploads them on the copy stream; a single frame takes the plain path.
     plain: one ihist_compute per frame with a plan per shape, its upload on
     the copy stream into one of two staging buffers.  Queries: rectangles
     up, Eq. 2 launch and rows back, all on a high-priority query stream.
-    Output histograms come from torch's allocator on the compute stream and
-    are returned to it on eviction.
+    Output histograms come from torch's allocator on the compute stream the
+    first time a shape is seen; evicted ones are kept per shape and reused.
     """
 
     def __init__(self, mode="batched", nslots=64, max_shape=(1080, 1920, 64), query_slots=8, max_rects=10000,
@@ -486,10 +496,7 @@ class GpuExecutor:
             for _ in range(4):
                 ins = [torch.empty((h, w), dtype=torch.uint8, device="cuda") for _ in range(nslots)]
                 outs = [torch.empty((b, h, w), dtype=torch.int32, device="cuda") for _ in range(1)] * nslots
-                # one CTA slot per SM stays free, so a query launched on the
-                # high-priority stream starts while a batch is running instead
-                # of waiting for the whole persistent launch to end
-                self.batches.append(ihist.Batch(ins, b, outs=outs, tune={"ctas_per_sm": 3}))
+                self.batches.append(ihist.Batch(ins, b, outs=outs))
                 self.inputs.append(ins)
             del outs
         self.next_batch = 0
@@ -736,9 +743,9 @@ def serve(mode="batched", duration_s=2.0, budget_gb=40.0, seed=None, frame_rate=
         # the same requests, arriving 1000 times faster than the server can take them
         for r in reqs:
             r.t_arrival *= 1e-3
-    ex = GpuExecutor(mode, max_rects=max(1, rects_per_query), trace=trace, keep_results=False)
+    ex = GpuExecutor(mode, nslots=128, max_rects=max(1, rects_per_query), trace=trace, keep_results=False)
     ex.warm(sorted({(r.h, r.w, r.nbins) for r in reqs if isinstance(r, FrameRequest)}))
-    srv = Server(ex, int(budget_gb * (1 << 30)), mode=mode, keep_results=False)
+    srv = Server(ex, int(budget_gb * (1 << 30)), max_batch=128, mode=mode, keep_results=False)
     ex.start()
     t0 = time.perf_counter()
     srv.run(reqs, ex.clock)

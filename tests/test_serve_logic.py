@@ -217,3 +217,20 @@ def test_store_evictable_bytes_track_every_change():
         assert set(store.lru) == {k for k, e in store.entries.items() if e[1] == 0 and e[2]}, step
         assert store.used == sum(e[0] for e in store.entries.values()) <= budget_bytes
     assert evicted
+
+
+def test_busy_gpu_holds_partial_batches_until_launches_drain():
+    # a burst of 100 frames, 16 per shared launch: while two launches are in
+    # flight the rest wait to fill whole launches, so only the last is partial
+    ex = serve.FakeExecutor(frame_latency=2e-3)
+    srv = serve.Server(ex, budget_bytes=1 << 30, max_batch=16, min_batch=4)
+    done = srv.run(frames(100), Clock())
+    assert len(done) == 100 and all(d.status == "ok" for d in done)
+    sizes = [len(l[1]) for l in ex.launches if l[0] == "frames"]
+    assert sizes == [16] * 6 + [4]
+    # spaced arrivals (5 ms apart, each frame done in 2 ms) go out alone at once
+    ex = serve.FakeExecutor(frame_latency=2e-3)
+    srv = serve.Server(ex, budget_bytes=1 << 30, max_batch=16, min_batch=4)
+    done = srv.run(frames(10, dt=5e-3), Clock())
+    assert [len(l[1]) for l in ex.launches if l[0] == "frames"] == [1] * 10
+    assert max(d.t_launch - d.t_arrival for d in done) < 1e-3
