@@ -81,7 +81,11 @@ typedef struct ihist_plan_s *ihist_plan_t;
  *   groups_per_cta  bin groups one CTA serves side by side (warps = groups
  *                   x ceil(ceil(w/128)/m), at most 16 in all; frames split
  *                   into width segments count the warps of one segment);
- *                   narrow frames fill a CTA this way
+ *                   narrow frames fill a CTA this way.  Pixel-major output
+ *                   with every group in the CTA (8 or 16 bins per CTA,
+ *                   nbins / 4 a power of two) stores whole pixel records:
+ *                   the default for 2 to 4 groups when those items still
+ *                   fill a wave of CTAs, and in batches
  *   ctas_per_sm     persistent grid = ctas_per_sm x SMs (0 = occupancy limit)
  *   timeout_us      limit of each carry wait before it gives up and latches
  *                   IHIST_ERR_LOOKBACK_TIMEOUT (default 2,000,000 us)
@@ -226,8 +230,10 @@ int ihist_compute(ihist_plan_t plan, const uint8_t *d_in, size_t in_pitch, uint3
  * x = column.  d_hist_out: n x nbins uint32, row i = histogram of rect i.
  * A rectangle with x0 > x1, y0 > y1 or a corner outside the frame yields a
  * zero row and latches IHIST_ERR_BAD_RECT.  n == 0 is a no-op.  The
- * launch may start while the kernel before it on the stream finishes; it
- * waits for that kernel before reading anything. */
+ * launch may start while the kernel before it on the stream finishes when
+ * that kernel is one of this library's (a scan): it then reads d_rects at
+ * once (no library kernel writes rectangles) and d_hist only after that
+ * kernel completed.  After any other kernel it starts when that one ends. */
 int ihist_query(ihist_plan_t plan, const uint32_t *d_hist, const int32_t *d_rects, int n,
                 uint32_t *d_hist_out, void *stream);
 

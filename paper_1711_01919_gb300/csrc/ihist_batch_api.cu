@@ -41,13 +41,36 @@ constexpr int kBatchWarps = 16;  // default warps per CTA of the batched kernel
 // that hold columns, smaller m on ties.  A frame wider than warps x max_m
 // chunks is split into width segments of equal chunk counts (one work item
 // each, see the scan kernel); segments are used only when no tiling without
-// them exists.  Returns false if no tiling fits max_ncg.
+// them exists, or for the whole-record pixel-major tilings below.  Returns
+// false if no tiling fits max_ncg.
 bool batch_frame_tiling(int h, int w, int nbins, int layout, int G, int R_req, int max_m, int max_ncg,
                         int warps, FrameDesc *f) {
   const int nchunks = (w + kChunk - 1) / kChunk;
   const int ngroups = (nbins + G - 1) / G;
   double best = -1.0;
   int bm = 1, bwpg = nchunks, bgpc = 1, bsegs = 1;
+  // Pixel-major frames of two to four bin groups whose records the scan
+  // kernel can store whole (its record path): take a tiling with every
+  // group in the CTA when one fits, width segments allowed (64 pixel-major
+  // 1080p x 64 frames: 7.95 -> 7.85 ms).
+  if (pm_staged(layout, G) && ngroups >= 2 && ngroups <= 4 && ngroups <= warps && pm_record_bins(nbins)) {
+    const int per = warps / ngroups;  // warps of one group
+    for (int m = 1; m <= max_m; m <<= 1) {
+      const int wpg_all = (nchunks + m - 1) / m;
+      const int nsegs = (wpg_all + per - 1) / per;
+      const int wpg = (wpg_all + nsegs - 1) / nsegs;
+      const int ncl = std::min(nchunks, wpg * m);
+      if (ncl * ngroups > max_ncg) continue;
+      const double util = (double)nchunks * ngroups / ((double)nsegs * warps * m);
+      if (util > best + 1e-9) {
+        best = util;
+        bm = m;
+        bwpg = wpg;
+        bgpc = ngroups;
+        bsegs = nsegs;
+      }
+    }
+  }
   for (int pass = 0; pass < 2 && best < 0.0; ++pass) {
     for (int m = 1; m <= max_m; m <<= 1) {
       const int wpg_all = (nchunks + m - 1) / m;

@@ -21,16 +21,28 @@ __global__ void __launch_bounds__(256) query_kernel(const uint32_t *__restrict__
                                                      const int32_t *__restrict__ rects,
                                                      unsigned int total,
                                                      uint32_t *__restrict__ out, Ctrl *ctrl) {
-  // launched with programmatic stream serialization: the histogram is read
-  // only once the grid before (normally the scan that wrote it) completed
-  griddep_wait_and_release();
+  // Launched with programmatic stream serialization: the histogram is read
+  // only once the grid before (normally the scan that wrote it) completed.
+  // The grids that let this one start early are the library's own, which
+  // never write rectangles, so each thread's first rectangle is read before
+  // that wait.
   const size_t plane = (size_t)H * (size_t)W;
-  for (unsigned int p = blockIdx.x * blockDim.x + threadIdx.x; p < total;
-       p += gridDim.x * blockDim.x) {
+  const unsigned int stride = gridDim.x * blockDim.x;
+  unsigned int p = blockIdx.x * blockDim.x + threadIdx.x;
+  int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
+  auto load_rect = [&](unsigned int pp) {
+    const size_t r4 = 4 * (size_t)(pp / (unsigned)B);
+    x0 = __ldg(rects + r4 + 0);
+    y0 = __ldg(rects + r4 + 1);
+    x1 = __ldg(rects + r4 + 2);
+    y1 = __ldg(rects + r4 + 3);
+  };
+  if (p < total) load_rect(p);
+  griddep_wait_and_release();
+  for (; p < total; p += stride) {
+    if (p != blockIdx.x * blockDim.x + threadIdx.x) load_rect(p);
     const unsigned int r = p / (unsigned)B;
     const int b = (int)(p - r * (unsigned)B);
-    const int x0 = __ldg(rects + 4 * (size_t)r + 0), y0 = __ldg(rects + 4 * (size_t)r + 1);
-    const int x1 = __ldg(rects + 4 * (size_t)r + 2), y1 = __ldg(rects + 4 * (size_t)r + 3);
     const bool ok = (0 <= x0) & (x0 <= x1) & (x1 < W) & (0 <= y0) & (y0 <= y1) & (y1 < H);
     uint32_t v = 0u;
     if (ok) {

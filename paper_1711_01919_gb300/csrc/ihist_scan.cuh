@@ -240,6 +240,73 @@ __device__ __forceinline__ void emit_pixel_major_staged(const FrameDesc &f, uint
   __syncwarp();  // the next row may overwrite the staging area
 }
 
+// Pixel-major rows when one CTA owns every bin of its pixels (gpc groups of
+// G bins covering B, with B / 4 a power of two): the gpc warps that hold
+// the same 128 columns, one per bin group, put their counts into one shared
+// area of whole pixel records (B words each), then store the row's records
+// together as one contiguous run of H, so each warp store writes 512
+// contiguous bytes.  A record is kept as U = B / 4 16-byte units, unit j of
+// pixel p at p * U + (j ^ ((p / 4) mod U)): eight consecutive lanes hit
+// eight distinct 16-byte bank groups when writing (lane -> its 4 pixels)
+// and when reading (consecutive units).  Two named barriers per row (id
+// bar_id, the gpc warps) order the writes before the reads and the reads
+// before the next row's writes.
+template <int G, bool VEC>
+__device__ __forceinline__ void emit_pixel_major_record(const FrameDesc &f, uint4 *rec, const uint32_t (&acc)[G][4],
+                                                        int lane, int lg, int cbase, int y, int bar_id, int nthr,
+                                                        Ctrl *ctrl) {
+  const uint32_t *out_end = f.out + (size_t)f.H * f.W * f.B;
+  (void)out_end;
+  (void)ctrl;
+  constexpr int GQ = G / 4;
+  const int U = f.B >> 2;
+  const int um = U - 1;
+  const int lu = __ffs(U) - 1;
+#pragma unroll
+  for (int r = 0; r < GQ; ++r) {
+    const int j = lg * GQ + r;
+    if (j < U) {
+      const int js = j ^ (lane & um);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        rec[(4 * lane + i) * U + js] = make_uint4(acc[4 * r][i], acc[4 * r + 1][i], acc[4 * r + 2][i], acc[4 * r + 3][i]);
+    }
+  }
+  named_bar_sync(bar_id, nthr);
+  const int nu = min(kChunk, f.W - cbase) << lu;
+  uint32_t *o0 = f.out + ((size_t)y * f.W + cbase) * f.B;
+  for (int u = lg * 32 + lane; u < nu; u += nthr) {
+    const int p = u >> lu, j = u & um;
+    const uint4 v = rec[p * U + (j ^ ((p >> 2) & um))];
+    uint32_t *o = o0 + 4 * u;
+    if (IHIST_GUARD(ctrl, o >= f.out && o + 4 <= out_end)) {
+      if (VEC) {
+        st_stream_v4(o, v.x, v.y, v.z, v.w);
+      } else {
+        st_stream(o, v.x);
+        st_stream(o + 1, v.y);
+        st_stream(o + 2, v.z);
+        st_stream(o + 3, v.w);
+      }
+    }
+  }
+  named_bar_sync(bar_id, nthr);
+}
+
+// Bin counts whose pixel records the whole-record path can hold: B / 4
+// 16-byte units, a power of two.
+__host__ __device__ inline bool pm_record_bins(int B) {
+  const int U = B >> 2;
+  return (B & 3) == 0 && U > 0 && (U & (U - 1)) == 0;
+}
+
+// Whether a pixel-major frame takes the whole-record path above (uniform
+// over the CTA: it depends only on the frame and the tiling).
+template <int G>
+__host__ __device__ inline bool pm_record(int layout, int B, int gpc, int ngroups) {
+  return layout == 1 && G >= 8 && gpc > 1 && gpc == ngroups && gpc * G >= B && pm_record_bins(B);
+}
+
 template <int G, int MMAX, bool TMA, bool VEC, bool LUT, bool WINDOW>
 __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorMap *tmap,
                                              unsigned int it, uint32_t epoch, Ctrl *ctrl,
@@ -447,11 +514,18 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
   }
 
   // ---- per chunk: look-back, publish inclusive row, emit ----
+  // Whole-record pixel-major rows: the warps of every bin group holding the
+  // same columns (same wg, same chunks, same rows) meet at named barrier
+  // 1 + wg, so each of them runs the same barrier sequence per chunk: one
+  // vote before the rows (taken on every path) and two per row.
+  const bool record = s_stage != nullptr && pm_record<G>(f.layout, f.B, f.gpc, f.ngroups);
+  const int rec_bar = 1 + wg, rec_thr = 32 * f.gpc;
   for (int cc = 0; cc < my_m; ++cc) {
     const int c = c_begin + cc;
     const unsigned int ci = ci0 + c;
     const int x = c * kChunk + 4 * lane;
-    if (!IHIST_GUARD(ctrl, ci < nci)) continue;
+    const bool ci_ok = IHIST_GUARD(ctrl, ci < nci);
+    if (!ci_ok && !record) continue;
 
     uint32_t left[G];  // band-count sums left of the chunk, from aggregates
     uint32_t s16[GQ][4][2];
@@ -462,7 +536,7 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
 #pragma unroll
       for (int i = 0; i < 4; ++i) s16[q][i][0] = s16[q][i][1] = 0u;
 
-    bool poisoned = !stage_ok;
+    bool poisoned = !stage_ok || !ci_ok;
     bool summed = false;
     int incl_at = -1;  // band whose inclusive row ends the look-back
     // Look back over the bands above.  The band just above has usually
@@ -651,13 +725,16 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
       if (publish && lane == 0) st_release_gpu(f.flags + ci, (epoch << 2) | kStateIncl);
 
       // ---- emit the band's rows of this chunk ----
+      bool emit_ok = true;
       if (staged != c) {
-        if (!stage_tile<TMA>(f, tmap, tile, bar, phase, y0, nrows, c, lane, timeout_ns)) {
-          if (lane == 0) latch_status(ctrl, kStatusTimeout);
-          continue;
-        }
-        staged = c;
+        emit_ok = stage_tile<TMA>(f, tmap, tile, bar, phase, y0, nrows, c, lane, timeout_ns);
+        if (emit_ok)
+          staged = c;
+        else if (lane == 0)
+          latch_status(ctrl, kStatusTimeout);
       }
+      if (record) emit_ok = named_bar_and(rec_bar, rec_thr, emit_ok);
+      if (!emit_ok) continue;
       const size_t plane = (size_t)f.H * (size_t)f.W;
       const bool last_chunk = (cc == my_m - 1);  // its row carries are not needed again
       for (int yl = 0; yl < nrows; ++yl) {
@@ -758,8 +835,12 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
             }
           }
         } else if (G >= 8 && s_stage != nullptr) {
-          emit_pixel_major_staged<G, VEC>(f, s_stage + (size_t)w * (kChunk * G / 4), acc, lane, c * kChunk, y, g,
-                                          ctrl);
+          if (record)
+            emit_pixel_major_record<G, VEC>(f, s_stage + (size_t)wg * (kChunk * G / 4) * f.gpc, acc, lane, lg,
+                                            c * kChunk, y, rec_bar, rec_thr, ctrl);
+          else
+            emit_pixel_major_staged<G, VEC>(f, s_stage + (size_t)w * (kChunk * G / 4), acc, lane, c * kChunk, y, g,
+                                            ctrl);
         } else {
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -784,8 +865,9 @@ __device__ __forceinline__ void process_item(const FrameDesc &f, const CUtensorM
         }
       }
     } else {
-      if (publish && lane == 0) st_release_gpu(f.flags + ci, (epoch << 2) | kStatePoison);
+      if (ci_ok && publish && lane == 0) st_release_gpu(f.flags + ci, (epoch << 2) | kStatePoison);
       if (!stage_ok && lane == 0) latch_status(ctrl, kStatusTimeout);
+      if (record) (void)named_bar_and(rec_bar, rec_thr, false);  // the vote the rows would take
     }
   }
 }
@@ -821,6 +903,9 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
   if (TMA) mbar_init_fence();
   uint32_t phase = 0;
   bool dep_pending = true;  // griddepcontrol.wait not yet done by this thread
+  // A grid of one CTA per item (frames below one wave): the first draws
+  // take every ticket, so no CTA draws a second one.
+  const bool one_each = gridDim.x >= f.nitems;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(&ctrl->ticket, 1u);
     __syncthreads();
@@ -839,6 +924,7 @@ __global__ void __launch_bounds__(512, (G <= 8 ? 2 : 1))
     process_item<G, MMAX, TMA, VEC, LUT, true>(f, &tmap, it, epoch, ctrl, timeout_ns, s_tiles, s_row, s_ctot,
                                          s_bar, s_lut, s_stage, phase, dep_pending);
     __syncthreads();
+    if (one_each) break;
   }
   if (threadIdx.x == 0) {
     __threadfence();

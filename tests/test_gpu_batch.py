@@ -252,6 +252,26 @@ def test_pixel_major_batch_defaults_to_16_bin_groups():
         check_batch(batch, imgs, nbins, [1] * len(shapes))
 
 
+@pytest.mark.parametrize("tune", [None, {"warps_per_cta": 16}, {"warps_per_cta": 8, "rows_per_band": 5}])
+def test_pixel_major_batch_stores_whole_records(tune):
+    # pixel-major frames whose bin groups all fit one CTA (B = 32, 64, 128
+    # with 16-bin groups) take the whole-record rows, with width segments
+    # where the CTA's warps cannot span the frame; a bin-major frame and a
+    # pixel-major one outside that path (16 bins: one group; 100 bins:
+    # records of 25 units) share the launch
+    shapes = [(200, 1920, 64, 1), (150, 700, 32, 1), (61, 1000, 128, 1), (90, 333, 16, 1), (45, 640, 64, 0),
+              (37, 131, 100, 1)]
+    imgs = [synth.uniform_frame(5000 + i, h, w) for i, (h, w, b, l) in enumerate(shapes)]
+    nbins = [b for (h, w, b, l) in shapes]
+    layouts = [l for (h, w, b, l) in shapes]
+    with ihist.Batch([torch.from_numpy(x).cuda() for x in imgs], nbins, layouts, tune=tune) as batch:
+        assert batch.tune["bins_per_cta"] == 16
+        for _ in range(2):
+            batch.compute()
+            assert batch.status() == ihist.IHIST_OK
+            check_batch(batch, imgs, nbins, layouts)
+
+
 def test_autotuned_layout_and_launch_shape_give_exact_batches(tmp_path, monkeypatch):
     # the autotuner times both layouts (each with its own tuned launch shape)
     # with and without a query load; whatever it picks computes exactly

@@ -69,6 +69,30 @@ def test_width_segment_timeout_is_bounded_and_reported(skip_band):
             assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(nbins, h, w), ref)
 
 
+@pytest.mark.parametrize("skip_band", [0, 2, 5])
+def test_pixel_major_record_timeout_is_bounded_and_reported(skip_band):
+    # whole-record pixel-major rows: the four bin groups' warps of a column
+    # range meet at named barriers, so a timed-out wait in one of them must
+    # still take its vote; the launch ends within the timeout, reports it,
+    # and the next launch is exact
+    h, w, nbins = 48, 700, 64
+    img = synth.uniform_frame(9, h, w)
+    base = {"bins_per_cta": 16, "groups_per_cta": 4, "chunks_per_warp": 1, "rows_per_band": 8}
+    ref = oracle.integral_histogram(img, nbins).transpose(1, 2, 0)
+    with ihist.Plan(h, w, nbins, 1, tune=dict(base, fault_skip_band=skip_band + 1, timeout_us=20000)) as plan:
+        d_img = torch.from_numpy(img).cuda()
+        t0 = time.time()
+        plan.compute(d_img)
+        st = plan.status()
+        assert time.time() - t0 < 5.0
+        assert st == ihist.IHIST_ERR_LOOKBACK_TIMEOUT
+    with ihist.Plan(h, w, nbins, 1, tune=base) as plan:
+        for _ in range(2):
+            out = plan.compute(torch.from_numpy(img).cuda())
+            assert plan.status() == ihist.IHIST_OK
+            assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(h, w, nbins), ref)
+
+
 def test_plan_recovers_after_timeout_launch():
     # a plan whose previous launch timed out runs the next launch cleanly
     # (flags carry the launch epoch, so stale ones are ignored)

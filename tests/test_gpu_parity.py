@@ -120,6 +120,35 @@ def test_multi_group_ctas(h, w, nbins, tune, layout):
     assert_same(got, to_layout(ref, layout), "%s %dx%d B=%d" % (tune, h, w, nbins))
 
 
+# Pixel-major frames whose CTA owns every bin group (groups_per_cta =
+# number of groups, B / 4 a power of two) store whole pixel records: the
+# warps of one column range meet at a named barrier per row.  Records of
+# 4..64 16-byte units, 8 and 16 bins per group, ragged and unaligned widths
+# (scalar stores), width segments, one-row bands and pitched input.
+RECORD_CASES = [
+    (300, 640, 64, {"bins_per_cta": 16, "groups_per_cta": 4, "chunks_per_warp": 1}, 0),
+    (130, 1920, 64, {"bins_per_cta": 16, "groups_per_cta": 4, "chunks_per_warp": 2, "rows_per_band": 29}, 0),
+    (77, 333, 32, {"bins_per_cta": 16, "groups_per_cta": 2}, 0),
+    (50, 200, 16, {"bins_per_cta": 8, "groups_per_cta": 2, "rows_per_band": 7}, 0),
+    (40, 500, 128, {"bins_per_cta": 16, "groups_per_cta": 8, "chunks_per_warp": 1}, 0),
+    (20, 300, 256, {"bins_per_cta": 16, "groups_per_cta": 16, "rows_per_band": 6}, 0),
+    (64, 256, 32, {"bins_per_cta": 16, "groups_per_cta": 2, "rows_per_band": 1}, 0),
+    (90, 1000, 64, {"bins_per_cta": 8, "groups_per_cta": 8, "chunks_per_warp": 1, "rows_per_band": 11}, 0),
+    (60, 700, 64, {"bins_per_cta": 16, "groups_per_cta": 4}, 7),
+]
+
+
+@pytest.mark.parametrize("h,w,nbins,tune,pitch_pad", RECORD_CASES)
+def test_pixel_major_whole_records(h, w, nbins, tune, pitch_pad):
+    img = synth.uniform_frame(h * 13 + w * 7 + nbins, h, w)
+    ref = to_layout(oracle.integral_histogram(img, nbins), 1)
+    got = run_gpu(img, nbins, layout=1, tune=tune, pitch_pad=pitch_pad, offset=3 if pitch_pad else 0)
+    assert_same(got, ref, "%s %dx%d B=%d pad %d" % (tune, h, w, nbins, pitch_pad))
+    img = synth.gradient_frame(h + w + nbins, h, w)
+    assert_same(run_gpu(img, nbins, layout=1, tune=tune), to_layout(oracle.integral_histogram(img, nbins), 1),
+                "gradient %s" % tune)
+
+
 def test_infeasible_tiling_is_rejected():
     # 8 warps x 255 rows x 128 bytes of staged input exceed shared memory
     with pytest.raises(ihist.IhistError) as e:
