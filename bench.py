@@ -107,6 +107,16 @@ def make_rects() -> np.ndarray:
     return synth.rects(synth.workload_seed(2) + 1, NRECTS, H, W)
 
 
+def fnv1a64_of_hashes(hashes) -> int:
+    """FNV-1a 64 over the little-endian bytes of a list of 64-bit frame hashes
+    (one value for a set of frames)."""
+    h = 0xCBF29CE484222325
+    for v in hashes:
+        for byte in int(v).to_bytes(8, "little"):
+            h = ((h ^ byte) * 0x100000001B3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
 def algorithmic_bytes_per_frame() -> int:
     return H * W * NBINS * 4 + H * W  # uint32 output written once + uint8 frame read once
 
@@ -456,7 +466,9 @@ def serving_report(seconds: float) -> dict:
     return out
 
 
-def _median_ms(fn, stream, reps: int = 5, warm: int = 3) -> float:
+def _time_ms(fn, stream, reps: int = 50, warm: int = 10) -> dict:
+    """Median and min of `reps` CUDA-event timings of fn on `stream` after
+    `warm` untimed runs, each bracketed by device synchronisations."""
     import torch
     for _ in range(warm):
         fn()
@@ -469,12 +481,16 @@ def _median_ms(fn, stream, reps: int = 5, warm: int = 3) -> float:
         b.record(stream)
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(b))
-    return statistics.median(ts)
+    return {"median": statistics.median(ts), "min": min(ts)}
+
+
+def _median_ms(fn, stream, reps: int = 50, warm: int = 10) -> float:
+    return _time_ms(fn, stream, reps, warm)["median"]
 
 
 def configs_report(stream, peak: float) -> dict:
-    """The other workloads of the method, each timed on its own (median of 5
-    after 3 warm-ups, CUDA events): one 640x480 frame with 32 bins and 1000
+    """The other workloads of the method, each timed on its own (median and
+    min of 50 after 10 warm-ups, CUDA events): one 640x480 frame with 32 bins and 1000
     queries per launch pair (8 frames and 8 outputs in rotation, 315 MB > L2);
     a 256-frame batch of uneven size (320x240 .. 1920x1080, 16/32/64 bins) in
     one persistent launch, default and autotuned tiling, the autotuned one
@@ -488,7 +504,10 @@ def configs_report(stream, peak: float) -> dict:
     # 640x480, 32 bins, 1000 queries
     h, w, b = 480, 640, 32
     seed = synth.workload_seed(1)
-    fr = [torch.from_numpy(synth.uniform_frame(synth.substream_seed(seed, i), h, w)).cuda() for i in range(8)]
+    host_fr = [synth.uniform_frame(synth.substream_seed(seed, i), h, w) for i in range(8)]
+    rep["input_fnv1a64"] = {"vga_640x480_frames": [hex(synth.fnv1a64_rows(x)) for x in host_fr]}
+    fr = [torch.from_numpy(x).cuda() for x in host_fr]
+    del host_fr
     ou = [torch.empty((b, h, w), dtype=torch.int32, device="cuda") for _ in range(8)]
     rects = torch.from_numpy(synth.rects(seed + 1, 1000, h, w)).cuda()
     q = torch.empty((1000, b), dtype=torch.int32, device="cuda")
@@ -501,17 +520,23 @@ def configs_report(stream, peak: float) -> dict:
                 for i in range(64):
                     ihist.ihist_compute(plan.handle, fr[i % 8].data_ptr(), w, ou[i % 8].data_ptr(), s)
                     ihist.ihist_query(plan.handle, ou[i % 8].data_ptr(), rects.data_ptr(), 1000, q.data_ptr(), s)
-            ms = _median_ms(vga, stream)
+            tm = _time_ms(vga, stream)
+            ms = tm["median"]
             if plan.status() != ihist.IHIST_OK:
                 raise SystemExit("device status error in the 640x480 run")
             rep[label] = {"frames_per_s": 64e3 / ms, "us_per_frame": ms * 1e3 / 64,
+                          "us_per_frame_min": tm["min"] * 1e3 / 64,
                           "gbs": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak,
                           "form": "ihist_compute + ihist_query per frame" + (", overlap=1" if tune else ""),
                           "tile": plan.tune}
     del fr, ou, rects, q
     # 256 uneven frames in one launch
     specs = synth.uneven_batch_specs(synth.workload_seed(3), 256)
-    fr = [torch.from_numpy(synth.uniform_frame(sd, h, w)).cuda() for (h, w, nb, sd) in specs]
+    host_fr = [synth.uniform_frame(sd, h, w) for (h, w, nb, sd) in specs]
+    rep["input_fnv1a64"]["uneven_256_frames_combined"] = hex(fnv1a64_of_hashes(
+        [synth.fnv1a64_rows(x) for x in host_fr]))
+    fr = [torch.from_numpy(x).cuda() for x in host_fr]
+    del host_fr
     ou = [torch.empty((nb, h, w), dtype=torch.int32, device="cuda") for (h, w, nb, sd) in specs]
     nbs = [nb for (h, w, nb, sd) in specs]
     byts = sum(h * w * nb * 4 + h * w for (h, w, nb, sd) in specs)
@@ -522,10 +547,11 @@ def configs_report(stream, peak: float) -> dict:
     names = {ihist.IHIST_BIN_MAJOR: "bin-major", ihist.IHIST_PIXEL_MAJOR: "pixel-major", ihist.IHIST_QUAD_MAJOR: "quad-major"}
     for label, tune, layout in (("default", None, ihist.IHIST_BIN_MAJOR), ("autotuned", auto_tune, auto_layout)):
         with ihist.Batch(fr, nbs, [layout] * len(fr), outs=ou, tune=tune or None) as batch:
-            ms = _median_ms(batch.compute, stream)
+            tm = _time_ms(batch.compute, stream)
+            ms = tm["median"]
             if batch.status() != ihist.IHIST_OK:
                 raise SystemExit("device status error in the uneven batch")
-            entry[label] = {"ms": ms, "frames_per_s": 256e3 / ms, "gbs": byts / ms / 1e6,
+            entry[label] = {"ms": ms, "ms_min": tm["min"], "frames_per_s": 256e3 / ms, "gbs": byts / ms / 1e6,
                             "frac": byts / ms / 1e6 / peak, "items": batch.items(), "layout": names[layout]}
             if label == "autotuned":
                 entry[label]["tune"] = auto_tune
@@ -545,18 +571,22 @@ def configs_report(stream, peak: float) -> dict:
     # 8192 x 8192, 128 bins, 2^20 queries
     h = w = 8192
     b = 128
-    img = torch.from_numpy(synth.sinusoid_frame(synth.workload_seed(5), h, w)).cuda()
+    host_img = synth.sinusoid_frame(synth.workload_seed(5), h, w)
+    rep["input_fnv1a64"]["sinusoid_8192x8192"] = hex(synth.fnv1a64_rows(host_img))
+    img = torch.from_numpy(host_img).cuda()
+    del host_img
     out = torch.empty((b, h, w), dtype=torch.int32, device="cuda")
     rects = torch.from_numpy(synth.rects(synth.workload_seed(5) + 1, 1 << 20, h, w)).cuda()
     q = torch.empty((1 << 20, b), dtype=torch.int32, device="cuda")
     with ihist.Plan(h, w, b) as plan:
         clocks = ClockSampler(nvml_bus_id(torch.cuda.current_device()))
         clocks.start()
-        ms = _median_ms(lambda: ihist.ihist_compute(plan.handle, img.data_ptr(), w, out.data_ptr(), s), stream,
-                        reps=3, warm=2)
+        tm = _time_ms(lambda: ihist.ihist_compute(plan.handle, img.data_ptr(), w, out.data_ptr(), s), stream)
+        ms = tm["median"]
         clk = clocks.stop(None)
-        qms = _median_ms(lambda: ihist.ihist_query(plan.handle, out.data_ptr(), rects.data_ptr(), 1 << 20,
-                                                   q.data_ptr(), s), stream, reps=3, warm=2)
+        tq = _time_ms(lambda: ihist.ihist_query(plan.handle, out.data_ptr(), rects.data_ptr(), 1 << 20,
+                                                q.data_ptr(), s), stream)
+        qms = tq["median"]
         sorted_ms = {}
         work = torch.empty((plan.query_work_bytes(1 << 20, 4),), dtype=torch.uint8, device="cuda")
         for bpp in (4, 8, 16):
@@ -565,7 +595,7 @@ def configs_report(stream, peak: float) -> dict:
             q2 = torch.empty_like(q)
             sorted_ms[bpp] = _median_ms(lambda: ihist.ihist_query_sorted(
                 plan.handle, out.data_ptr(), rects.data_ptr(), 1 << 20, q2.data_ptr(), bpp, work.data_ptr(),
-                work.numel(), s), stream, reps=3, warm=2)
+                work.numel(), s), stream)
             if not torch.equal(q2, q):
                 raise SystemExit("sorted and plain 8192x8192 queries differ")
             del q2
@@ -573,11 +603,11 @@ def configs_report(stream, peak: float) -> dict:
         if plan.status() != ihist.IHIST_OK:
             raise SystemExit("device status error in the 8192x8192 run")
         byts = h * w * b * 4 + h * w
-        rep["mp64_8192x8192_b128"] = {"scan_ms": ms, "gbs": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak,
+        rep["mp64_8192x8192_b128"] = {"scan_ms": ms, "scan_ms_min": tm["min"], "gbs": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak,
                                       "bytes_per_launch": byts, "traffic": profiled_traffic(PROFILE_MP64),
                                       "traffic_source": "ncu DRAM bytes of the same launch shape on the top rows "
                                                         "of the frame, scaled to 8192 rows (profiles/)",
-                                      "clocks": clk, "query_ms_2p20_rects": qms,
+                                      "clocks": clk, "query_ms_2p20_rects": qms, "query_ms_min": tq["min"],
                                       "query_sorted_ms_2p20_rects": {"bins_per_pass_%d" % k: v
                                                                      for k, v in sorted_ms.items()},
                                       "tile": plan.tune}
@@ -601,7 +631,7 @@ def query_gather_report(hist, query_ms: float, nrects: int, nbins: int, stream) 
     g.manual_seed(1711)
     idx = torch.randint(0, hist.numel(), (n,), device=hist.device, dtype=torch.int64, generator=g)
     flat = hist.view(-1)
-    ms = _median_ms(lambda: torch.take(flat, idx), stream, reps=3, warm=2)
+    ms = _median_ms(lambda: torch.take(flat, idx), stream)
     del idx
     gathers_per_s = n / (ms / 1e3)
     pairs = nrects * nbins
@@ -841,6 +871,8 @@ def main():
     ihist.load()
 
     frames = make_frames(rank)
+    from paper_1711_01919_gb300 import synth as _synth
+    input_hashes = [hex(_synth.fnv1a64_rows(f)) for f in frames]  # FNV-1a 64 of each generated frame
     rects = make_rects()
     d_frames = torch.from_numpy(frames).to(dev)
     # every frame queries the same rectangles: [frames][rects][4]
@@ -1049,6 +1081,7 @@ def main():
                 "layout": {ihist.IHIST_BIN_MAJOR: "bin-major", ihist.IHIST_PIXEL_MAJOR: "pixel-major",
                            ihist.IHIST_QUAD_MAJOR: "quad-major"}[layout],
                 "queries_per_frame": NRECTS,
+                "input_fnv1a64": input_hashes,
                 "form": "batched: one persistent scan launch over the %d resident frames + one query launch" % NFRAMES,
                 "parallelism": "replicas (one independent 64-frame sequence per GPU)" if world > 1 else "single GPU",
                 "l2": "no flush: each step writes %.1f GB of output, > 129 MB L2" % (NFRAMES * H * W * NBINS * 4 / 1e9),
