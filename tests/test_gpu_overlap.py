@@ -60,6 +60,8 @@ def test_tune_reports_overlap_and_rejects_bad_values():
     (333, 517, 20, 0, {"rows_per_band": 8}),
     (480, 640, 32, 1, {}),
     (97, 130, 5, 0, {"rows_per_band": 3, "ctas_per_sm": 1}),
+    (130, 3000, 16, 0, {"chunks_per_warp": 1}),  # two width segments per band
+    (300, 1920, 64, 1, {"bins_per_cta": 16, "groups_per_cta": 4, "chunks_per_warp": 1}),  # whole records
 ])
 def test_back_to_back_launches_equal_the_oracle(h, w, nbins, layout, tune):
     # 9 launches: both control blocks several times, distinct frames, a ring
