@@ -62,11 +62,13 @@ def parse_args():
                     help="simulated seconds of the serving workload per server mode (0 = skip)")
     ap.add_argument("--frames", type=int, default=64,
                     help="frames per step (64 = the workload; smaller only for profiler captures)")
-    ap.add_argument("--case", choices=("sequence", "mp64-slice", "query-slice"), default="sequence",
+    ap.add_argument("--case", choices=("sequence", "mp64-slice", "query-slice", "vga"), default="sequence",
                     help="mp64-slice: only a few launches of the 8192x8192 x 128-bin scan's launch shape "
                          "on the top --slice-rows rows (a profiler capture of that kernel at a few GB); "
                          "query-slice: the plain and the row-bucketed region query of 2^18 rectangles on "
-                         "the top 1024 rows of that frame (4 GiB of H)")
+                         "the top 1024 rows of that frame (4 GiB of H); vga: the 640x480 x 32-bin "
+                         "frames, ihist_compute + ihist_query of 1000 rectangles each, overlap=1, 64 "
+                         "frames per step (the per-frame launches a profiler lists)")
     ap.add_argument("--slice-rows", type=int, default=768)
     return ap.parse_args()
 
@@ -382,6 +384,43 @@ def run_query_slice(args) -> int:
         if plan.status() != ihist.IHIST_OK or not torch.equal(q1, q2):
             raise SystemExit("query slice: device status error or the two queries differ")
         print(json.dumps({"case": "query-slice", "rows": h, "W": w, "B": b, "rects": n, "ms": ms}), flush=True)
+    return 0
+
+
+def run_vga(args) -> int:
+    """64 frames of 640x480 with 32 bins per step, each ihist_compute (plan
+    tune overlap=1) followed by ihist_query of 1000 rectangles, 8 inputs and
+    8 outputs in rotation: the per-frame launch pairs of the 640x480
+    workload, for a profiler's launch list and captures."""
+    import torch
+
+    from paper_1711_01919_gb300 import build as cuda_build
+    from paper_1711_01919_gb300 import ihist, synth
+    cuda_build.build()
+    ihist.load()
+    h, w, b = 480, 640, 32
+    seed = synth.workload_seed(1)
+    fr = [torch.from_numpy(synth.uniform_frame(synth.substream_seed(seed, i), h, w)).cuda() for i in range(8)]
+    ou = [torch.empty((b, h, w), dtype=torch.int32, device="cuda") for _ in range(8)]
+    rects = torch.from_numpy(synth.rects(seed + 1, 1000, h, w)).cuda()
+    q = torch.empty((1000, b), dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    us = []
+    with ihist.Plan(h, w, b, tune={"overlap": 1}) as plan:
+        for k in range(args.warmup + args.steps):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            for i in range(64):
+                ihist.ihist_compute(plan.handle, fr[i % 8].data_ptr(), w, ou[i % 8].data_ptr(), s)
+                ihist.ihist_query(plan.handle, ou[i % 8].data_ptr(), rects.data_ptr(), 1000, q.data_ptr(), s)
+            e.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                us.append(a.elapsed_time(e) * 1e3 / 64)
+        if plan.status() != ihist.IHIST_OK:
+            raise SystemExit("vga case: device status error")
+        print(json.dumps({"case": "vga", "H": h, "W": w, "B": b, "rects": 1000, "us_per_frame": us}), flush=True)
     return 0
 
 
@@ -851,6 +890,8 @@ def main():
         return run_mp64_slice(args)
     if args.case == "query-slice":
         return run_query_slice(args)
+    if args.case == "vga":
+        return run_vga(args)
     import torch
     import torch.distributed as dist
 

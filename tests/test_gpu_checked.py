@@ -30,7 +30,9 @@ n = 0
 for (h, w, b, l, tune) in [(1, 1, 3, 0, None), (37, 131, 16, 0, None), (64, 257, 7, 1, None), (100, 1000, 64, 1, None),
                            (33, 2049, 100, 0, {"bins_per_cta": 8}), (130, 640, 64, 1, {"bins_per_cta": 8}),
                            (300, 4096, 8, 0, None), (17, 128, 256, 1, None), (37, 131, 16, 2, None),
-                           (130, 643, 64, 2, {"bins_per_cta": 16})]:
+                           (130, 643, 64, 2, {"bins_per_cta": 16}),
+                           (130, 700, 64, 1, {"bins_per_cta": 16, "groups_per_cta": 4, "chunks_per_warp": 1}),
+                           (40, 500, 128, 1, {"bins_per_cta": 16, "groups_per_cta": 8, "chunks_per_warp": 1})]:
     img = synth.uniform_frame(h + w + b, h, w)
     with ihist.Plan(h, w, b, l, tune=tune) as p:
         got = u32(p.compute(torch.from_numpy(img).cuda())).reshape(p.out_shape)
