@@ -330,7 +330,8 @@ def run_mp64_slice(args) -> int:
     img = torch.from_numpy(synth.sinusoid_frame(synth.workload_seed(5), 8192, w)[:h].copy()).cuda()
     out = torch.empty((b, h, w), dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
-    keep = {k: tune[k] for k in ("rows_per_band", "bins_per_cta", "chunks_per_warp", "groups_per_cta", "ctas_per_sm")}
+    keep = {k: tune[k] for k in ("rows_per_band", "bins_per_cta", "chunks_per_warp", "groups_per_cta", "ctas_per_sm",
+                                 "warps_per_cta")}
     with ihist.Plan(h, w, b, tune=keep) as plan:
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * (args.warmup + args.steps))]
         for k in range(args.warmup + args.steps):

@@ -99,8 +99,11 @@ typedef struct ihist_plan_s *ihist_plan_t;
  *                   and for frames wider than 8 warps can cover).  A frame
  *                   wider than 4 x warps_per_cta chunks of 128 columns (2 x
  *                   with 16 bins per CTA) is split into width segments.
- *                   Plans derive it from the tiling, ignore it on input
- *                   and report it in ihist_plan_get_tune.
+ *                   Plans: an upper bound on the warps of one CTA (1..16,
+ *                   0 = 16; frames wider than it x chunks_per_warp chunks
+ *                   split into width segments); ihist_plan_get_tune reports
+ *                   the warps the plan uses, which recreates the same
+ *                   tiling when passed back.
  *   overlap         plans: every ihist_compute (and ihist_query) is launched
  *                   with programmatic dependent launch, so its CTAs may
  *                   start while the kernel launched just before it on the

@@ -151,11 +151,11 @@ static int occupancy(ScanFn fn, int threads, size_t smem) {
 // bytes) x (warps per SM, up to 24) x (fraction of CTA bin groups in use).
 // Fields the caller fixed (non-zero) are kept.
 static void default_tiling(int h, int ngroups, int wpg, int G, int ncl, int nsegs, int sms, ScanFn fn,
-                           size_t optin, int layout, int *R, int *gpc) {
+                           size_t optin, int layout, int max_warps, int *R, int *gpc) {
   double best = -1.0;
   int best_r = *R ? *R : std::min(h, 8), best_g = *gpc ? *gpc : 1;
   const int g_lo = *gpc ? *gpc : 1;
-  const int g_hi = *gpc ? *gpc : std::max(1, std::min(ngroups, 16 / wpg));
+  const int g_hi = *gpc ? *gpc : std::max(1, std::min(ngroups, max_warps / wpg));
   for (int gp = g_lo; gp <= g_hi; ++gp) {
     const int NW = gp * wpg;
     const int ngsets = (ngroups + gp - 1) / gp;
@@ -233,6 +233,7 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   if (t.ctas_per_sm < 0 || t.ctas_per_sm > 32) return IHIST_ERR_INVALID_ARG;
   if (t.groups_per_cta < 0 || t.groups_per_cta > 16) return IHIST_ERR_INVALID_ARG;
   if (t.overlap != 0 && t.overlap != 1) return IHIST_ERR_INVALID_ARG;
+  if (t.warps_per_cta < 0 || t.warps_per_cta > 16) return IHIST_ERR_INVALID_ARG;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return IHIST_ERR_CUDA;
@@ -248,21 +249,34 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   // staged 159 us).
   const bool pm_wide = layout == IHIST_PIXEL_MAJOR && nbins >= 16 && nchunks <= 32 && !table;
   if (t.bins_per_cta == 0) t.bins_per_cta = layout == IHIST_PIXEL_MAJOR ? (pm_wide ? 16 : 8) : 4;
+  // Frames wider than 16 chunks (bin- and quad-major): one chunk per warp
+  // in CTAs of at most 8 warps, each band split into width segments, 48
+  // rows per band -- more, smaller CTAs per SM and the one-chunk kernel,
+  // against one 16-warp CTA spanning the width with several chunks per
+  // warp (measured per frame: 3840x2160 x 64 405 -> 357 us, 7680x4320 x 32
+  // 830 -> 690 us, 16384x2048 x 16 503 -> 374 us, 8192x8192 x 128 5.38 ->
+  // 5.01 ms; frames of up to 16 chunks are faster in one CTA).
+  if (nchunks > 16 && layout != IHIST_PIXEL_MAJOR && t.chunks_per_warp == 0 && t.warps_per_cta == 0) {
+    t.chunks_per_warp = 1;
+    t.warps_per_cta = 8;
+    if (t.rows_per_band == 0) t.rows_per_band = std::min(h, 48);
+  }
   if (t.chunks_per_warp == 0) {
     t.chunks_per_warp = nchunks <= 16 ? 1 : nchunks <= 32 ? 2 : nchunks <= 64 ? 4 : 8;
     if (t.bins_per_cta == 16) t.chunks_per_warp = std::min(t.chunks_per_warp, 2);  // the 16-bin kernels' limit
   }
+  const int cta_warps = t.warps_per_cta ? t.warps_per_cta : 16;  // upper bound on a CTA's warps
   if (t.timeout_us == 0) t.timeout_us = kDefaultTimeoutUs;
-  // Frames wider than 16 warps x m chunks (16 / groups_per_cta warps when
-  // that is given) split each band into width segments of equal chunk
-  // counts, one work item each (see the scan kernel).
+  // Frames wider than W warps x m chunks (W = warps_per_cta, default 16;
+  // W / groups_per_cta warps when that is given) split each band into width
+  // segments of equal chunk counts, one work item each (see the scan kernel).
   struct Split {
     int nsegs, wpg, cps, ncl;  // ncl: chunks of one CTA's group
   };
   auto split_for = [&](int gpc) {
     Split sp;
     const int wpg_all = (nchunks + t.chunks_per_warp - 1) / t.chunks_per_warp;
-    const int seg_warps = 16 / std::max(1, gpc);  // warps of one group, 16 per CTA in all
+    const int seg_warps = std::max(1, cta_warps / std::max(1, gpc));  // warps of one group
     sp.nsegs = (wpg_all + seg_warps - 1) / seg_warps;
     sp.wpg = (wpg_all + sp.nsegs - 1) / sp.nsegs;
     sp.cps = sp.wpg * t.chunks_per_warp;
@@ -271,7 +285,7 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   };
   Split sp = split_for(t.groups_per_cta);
   const int mmax = mmax_for(t.chunks_per_warp);
-  if (sp.wpg * std::max(1, t.groups_per_cta) > 16 || !scan_fn(t.bins_per_cta, mmax, true, true, table))
+  if (sp.wpg * std::max(1, t.groups_per_cta) > cta_warps || !scan_fn(t.bins_per_cta, mmax, true, true, table))
     return IHIST_ERR_UNSUPPORTED;
   size_t optin = 0;
   rc = prepare_kernels(t.bins_per_cta, mmax, dev, &optin, table);
@@ -282,7 +296,7 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
   if (t.rows_per_band == 0 || t.groups_per_cta == 0) {
     const bool gpc_free = t.groups_per_cta == 0;
     const int r_req = t.rows_per_band;
-    default_tiling(h, ngroups, sp.wpg, t.bins_per_cta, sp.ncl, sp.nsegs, sms, fn, optin, layout,
+    default_tiling(h, ngroups, sp.wpg, t.bins_per_cta, sp.ncl, sp.nsegs, sms, fn, optin, layout, cta_warps,
                    &t.rows_per_band, &t.groups_per_cta);
     // Staged pixel-major frames whose one-group items fit in one wave of
     // CTAs: one group per CTA, the most CTAs side by side (640x480 x 64,
@@ -290,7 +304,7 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
     // with 1; 640x480 x 32: 62.4 -> 61.3 us).
     if (gpc_free && t.groups_per_cta > 1 && pm_staged(layout, t.bins_per_cta)) {
       int R = r_req, g = 1;
-      default_tiling(h, ngroups, sp.wpg, t.bins_per_cta, sp.ncl, sp.nsegs, sms, fn, optin, layout, &R, &g);
+      default_tiling(h, ngroups, sp.wpg, t.bins_per_cta, sp.ncl, sp.nsegs, sms, fn, optin, layout, cta_warps, &R, &g);
       const size_t smem = smem_layout(sp.wpg, R, t.bins_per_cta, sp.ncl, true).bytes;
       const int occ = smem <= optin ? occupancy(fn, sp.wpg * 32, smem) : 0;
       const long long items = (long long)((h + R - 1) / R) * ngroups * sp.nsegs;
@@ -309,10 +323,10 @@ static int plan_create(int h, int w, int nbins, int layout, const ihist_tune_t *
         pm_staged(layout, t.bins_per_cta) && pm_record_bins(nbins) && !table) {
       const Split sr = split_for(ngroups);
       int R = r_req, g = ngroups;
-      default_tiling(h, ngroups, sr.wpg, t.bins_per_cta, sr.ncl, sr.nsegs, sms, fn, optin, layout, &R, &g);
+      default_tiling(h, ngroups, sr.wpg, t.bins_per_cta, sr.ncl, sr.nsegs, sms, fn, optin, layout, cta_warps, &R, &g);
       const int nw = sr.wpg * ngroups;
       const size_t smem = smem_layout(nw, R, t.bins_per_cta, sr.ncl * ngroups, true).bytes;
-      const int occ = (nw <= 16 && smem <= optin) ? occupancy(fn, nw * 32, smem) : 0;
+      const int occ = (nw <= cta_warps && smem <= optin) ? occupancy(fn, nw * 32, smem) : 0;
       const long long items = (long long)((h + R - 1) / R) * sr.nsegs;
       if (occ >= 1 && items >= (long long)occ * sms) {
         t.groups_per_cta = ngroups;

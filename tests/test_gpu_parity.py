@@ -93,6 +93,10 @@ TUNINGS = [
     {"rows_per_band": 9, "chunks_per_warp": 8, "bins_per_cta": 8},
     {"rows_per_band": 20, "chunks_per_warp": 2, "bins_per_cta": 16},
     {"rows_per_band": 12, "ctas_per_sm": 1},
+    # at most 8 (4) warps per CTA: frames wider than 8 (4) chunks per warp slot
+    # split into width segments
+    {"warps_per_cta": 8, "chunks_per_warp": 1, "rows_per_band": 10},
+    {"warps_per_cta": 4, "chunks_per_warp": 2, "bins_per_cta": 8},
 ]
 
 
@@ -147,6 +151,17 @@ def test_pixel_major_whole_records(h, w, nbins, tune, pitch_pad):
     img = synth.gradient_frame(h + w + nbins, h, w)
     assert_same(run_gpu(img, nbins, layout=1, tune=tune), to_layout(oracle.integral_histogram(img, nbins), 1),
                 "gradient %s" % tune)
+
+
+def test_warps_per_cta_caps_the_plan_and_round_trips():
+    with ihist.Plan(64, 3000, 16, 0, tune={"warps_per_cta": 8, "chunks_per_warp": 1}) as plan:
+        assert plan.tune["warps_per_cta"] <= 8
+        tune = plan.tune
+    with ihist.Plan(64, 3000, 16, 0, tune=tune) as again:
+        assert again.tune == tune  # the reported tiling recreates itself
+    with pytest.raises(ihist.IhistError) as e:
+        ihist.Plan(64, 256, 8, 0, tune={"warps_per_cta": 17})
+    assert e.value.code == ihist.IHIST_ERR_INVALID_ARG
 
 
 def test_infeasible_tiling_is_rejected():
