@@ -94,13 +94,18 @@ def job_throughput(frames_per_rank: int, steps: int, world: int, elapsed_ms: flo
     return world * frames_per_rank * steps / (elapsed_ms / 1000.0)
 
 
-def make_frames(rank: int, n: int = 0) -> np.ndarray:
+def make_frame(rank: int, f: int) -> np.ndarray:
+    """Frame f of rank `rank`'s sequence: gradient plus N(0, 20^2) noise, its
+    own substream of the workload's seed."""
     from paper_1711_01919_gb300 import synth
+    return synth.gradient_frame(synth.substream_seed(synth.workload_seed(2), rank * 100000 + f), H, W, SIGMA)
+
+
+def make_frames(rank: int, n: int = 0) -> np.ndarray:
     n = n or NFRAMES
-    seed = synth.workload_seed(2)
     out = np.empty((n, H, W), dtype=np.uint8)
     for f in range(n):
-        out[f] = synth.gradient_frame(synth.substream_seed(seed, rank * 100000 + f), H, W, SIGMA)
+        out[f] = make_frame(rank, f)
     return out
 
 
