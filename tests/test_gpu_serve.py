@@ -21,7 +21,7 @@ def _lib():
         pytest.skip("no CUDA device")
 
 
-def run_server(mode, duration=0.04, budget_gb=40.0, saturate=False):
+def run_server(mode, duration=0.04, budget_gb=40.0, saturate=False, nslots=16, max_batch=16):
     seed = synth.workload_seed(4)
     pool = {}
     for (w, h) in synth.BATCH_RESOLUTIONS:
@@ -30,9 +30,9 @@ def run_server(mode, duration=0.04, budget_gb=40.0, saturate=False):
     if saturate:
         for r in reqs:
             r.t_arrival = 0.0
-    ex = serve.GpuExecutor(mode, nslots=16, trace=True)  # NVTX ranges must not disturb anything
+    ex = serve.GpuExecutor(mode, nslots=nslots, trace=True)  # NVTX ranges must not disturb anything
     ex.warm(sorted({(r.h, r.w, r.nbins) for r in reqs if isinstance(r, serve.FrameRequest)}))
-    srv = serve.Server(ex, int(budget_gb * (1 << 30)), max_batch=16, mode=mode)
+    srv = serve.Server(ex, int(budget_gb * (1 << 30)), max_batch=max_batch, mode=mode)
     ex.start()
     srv.run(reqs, ex.clock)
     torch.cuda.synchronize()
@@ -131,5 +131,18 @@ def test_batched_server_under_a_small_budget_evicts_and_stays_exact():
     assert srv.store.evicted > 0
     assert srv.store.used <= 1 << 30
     assert all(d.status == "ok" for d in srv.done if d.kind == "frame")
+    assert check_alone(srv, reqs) == check_oracle(srv, reqs)
+    ex.close()
+
+
+def test_serving_configuration_saturated_stays_exact():
+    # the bench's server shape (128-frame slots, launches of up to 128
+    # frames from a ring of batches, the hold rule) with 0.2 s of requests
+    # all arriving at once: several large shared launches, evictions under
+    # the 40 GB budget, every resident histogram and query row exact
+    srv, ex, reqs = run_server("batched", duration=0.2, saturate=True, nslots=128, max_batch=128)
+    assert all(d.status == "ok" for d in srv.done if d.kind == "frame")
+    sizes = {int(k): v for k, v in srv.report(1.0)["launch_sizes"].items()}
+    assert max(sizes) >= 64 and sum(v for k, v in sizes.items() if k >= 8) >= 2
     assert check_alone(srv, reqs) == check_oracle(srv, reqs)
     ex.close()
